@@ -1,0 +1,32 @@
+"""CPU FP64 oracle for the two-scale (LSQP surrogate) HHG multigrid path.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product (the CUDA library and its
+Python binding) imports, links or executes anything in this package.  Only the
+tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` use
+it.  It shares no code with the CUDA path: the mesh, the element stiffness,
+the least-squares fit, the smoother, the transfers and the V-cycle are written
+here a second time, plainly, in NumPy/SciPy double precision.
+
+Paper: Bauer, Mohr, Ruede, Weismueller, Wittmann, Wohlmuth, "A two-scale
+approach for efficient on-the-fly operator assembly in massively parallel high
+performance multigrid codes" (arXiv:1608.06473).
+
+Modules
+-------
+mesh    Sec. 2.2: macro mesh of the spherical shell, regular refinement,
+        blending map Phi, HHG primitives and the canonical node order.
+fem     Sec. 2.2-2.3: exact P1 stiffness on the mapped mesh by global
+        element-wise assembly (the IFEM operator L_l).
+lsqp    Sec. 3.2 and 3.4: least-squares surrogate polynomials and the
+        surrogate operator (LSQP, L~_l).
+mg      Sec. 4 and Eq. 5.1: multicolour hybrid Gauss-Seidel smoother,
+        residual, transfers, coarse solve and the V(3,3) cycle.
+local   Per-macro stencil rows for sampled checks on shells too large to
+        assemble globally.
+
+Parity pins: every function here is checked by the ``-m "not gpu"`` tests
+against closed forms, invariants and the paper's printed numbers.  One part
+carries no such pin: the absolute error values of Table 4.1 (they depend on
+the macro mesh, the radii and the constant H, none of which the paper states);
+it is marked "parity unpinned" where it appears.
+"""
