@@ -1,0 +1,167 @@
+/*
+ * hhg.h -- C ABI of the GB300 two-scale HHG multigrid library (libhhg.so).
+ *
+ * Method: Bauer, Mohr, Ruede, Weismueller, Wittmann, Wohlmuth, "A two-scale
+ * approach for efficient on-the-fly operator assembly in massively parallel
+ * high performance multigrid codes" (arXiv:1608.06473).
+ *
+ * Problem (Sec. 2.1, Eq. 2.1): -Laplace(u) = f on the thick spherical shell
+ * r1 < |x| < r2, u = 0 on both spheres, P1 finite elements on a regularly
+ * refined tetrahedral macro mesh whose nodes are moved by the blending map
+ * Phi(x) = rho(x) x/|x| (Sec. 2.2).  The fine operator is applied matrix-free:
+ * either the exact stencil assembled on the fly from the 24 element matrices
+ * around every node (IFEM, Sec. 4.2.1), or the two-scale surrogate whose 15
+ * stencil weights are least-squares polynomials per macro cell (LSQP,
+ * Sec. 3.2-3.4), evaluated along fine-grid lines (Sec. 3.4, Eq. 5.4).
+ *
+ * Levels.  `L` is log2 of N, the number of intervals per macro edge
+ * (N = 2^L, L >= 2).  The paper's level l is L - 2 (N = 2^(l+2), Sec. 2.2).
+ * The coarsest level of every hierarchy is L = 2 (N = 4, one interior node
+ * per macro cell).
+ *
+ * Vectors.  A vector of level L holds one value per fine node in the
+ * canonical order: the macro vertices, then the N-1 nodes of every macro
+ * edge, then the (N-1)(N-2)/2 interior nodes of every macro face, then the
+ * (N-1)(N-2)(N-3)/6 interior nodes of every macro cell (i fastest, then j,
+ * then k).  hhg_num_nodes gives its length n_total.  `nrhs` vectors are
+ * stacked contiguously with stride n_total.  Entries at Dirichlet nodes (on
+ * r1 or r2) are ignored on input and written as 0 on output.
+ *
+ * Pointers.  Every vector argument may be device memory (e.g. a torch
+ * tensor's data_ptr) or host memory; host vectors are copied through
+ * library-owned device buffers on `stream`, and the call returns after the
+ * results have reached the host.  Device vectors are used in place and the
+ * call returns once the work is enqueued on `stream`, except where a host
+ * scalar output (norms, relres, cycles) is requested: then the call waits
+ * for the stream.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ *
+ * Ownership.  The caller owns every vector.  The library owns the hierarchy
+ * (index maps, halo copies, pre-assembled lower-primitive stencils,
+ * surrogate coefficients, per-level work vectors) and frees it in
+ * hhg_destroy.  All library allocations are charged against
+ * hbm_budget_bytes; a call that would exceed it returns HHG_ENOMEM without
+ * allocating.
+ *
+ * Errors.  Every call returns an hhg_status; on failure hhg_last_error()
+ * returns a message for the calling thread.  A CUDA error leaves the shell
+ * usable only for hhg_destroy.
+ *
+ * Threads.  One shell may be used from one host thread at a time; calls on
+ * the same shell that overlap on the GPU (different streams) race on its
+ * work vectors.
+ */
+#ifndef HHG_H
+#define HHG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hhg_shell hhg_shell;
+
+typedef enum {
+  HHG_OK = 0,
+  HHG_EINVAL = -1,     /* bad argument or descriptor */
+  HHG_ENOMEM = -2,     /* the HBM budget (or the device) has no room */
+  HHG_ECUDA = -3,      /* a CUDA call failed */
+  HHG_ENOTFIT = -4,    /* the surrogate was requested before hhg_fit_surrogate */
+  HHG_ENOCONV = -5,    /* max_cycles reached before rtol */
+  HHG_EDIVERGED = -6,  /* a residual norm became NaN or Inf */
+  HHG_ETIMEOUT = -7    /* a bounded device-side wait gave up */
+} hhg_status;
+
+typedef enum {
+  HHG_OP_IFEM = 0,     /* exact stencils, assembled on the fly (Sec. 4.2.1) */
+  HHG_OP_LSQP = 1      /* least-squares surrogate stencils (Sec. 3.2) */
+} hhg_op;
+
+typedef enum {
+  HHG_F64 = 0,
+  HHG_F32 = 1
+} hhg_dtype;
+
+/* Macro mesh and hierarchy (Sec. 2.2; macro counts of Sec. 4.1).
+ * The surface is an icosahedron refined `tang_refine` times (1:4 splits,
+ * midpoints projected to the sphere); `radial_layers` uniform layers between
+ * r_inner and r_outer; every prism is cut into three tetrahedra:
+ * 60 macro cells for (0, 1), 480 for (1, 2), 3840 for (2, 4). */
+typedef struct {
+  double r_inner;                /* r1 > 0 */
+  double r_outer;                /* r2 > r1 */
+  int tang_refine;               /* >= 0 */
+  int radial_layers;             /* >= 1 */
+  int fine_log2_intervals;       /* finest L (N = 2^L), 2..10 */
+  size_t hbm_budget_bytes;       /* 0 = no limit beyond the device */
+} hhg_shell_desc;
+
+/* Builds the macro mesh, its primitive graph and, for every level L = 2 ..
+ * fine_log2_intervals, the index maps, the halo maps and the exact stencils
+ * of all vertex, edge and face nodes (assembled from the element matrices of
+ * the adjacent macro cells, Sec. 2.3: lower primitives keep exact stencils).
+ * Work is enqueued on `stream` and completed before return. */
+hhg_status hhg_setup_shell(const hhg_shell_desc* desc, void* stream, hhg_shell** out);
+
+/* Frees everything the shell owns (NULL is accepted). */
+hhg_status hhg_destroy(hhg_shell* shell);
+
+/* n_total: vector length of level L; n_free: unknowns (non-Dirichlet). */
+hhg_status hhg_num_nodes(const hhg_shell* shell, int L, int64_t* n_total, int64_t* n_free);
+
+/* Mapped positions Phi(x) of all nodes of level L, canonical order, written
+ * to a host array of 3 * n_total doubles (x, y, z per node). */
+hhg_status hhg_node_coords(const hhg_shell* shell, int L, double* xyz_host);
+
+/* LSQP setup (Sec. 3.2, Table 4.3): for every macro cell and level L >= 3
+ * (paper l >= 1), the exact stencils at the sampling set
+ * S_l = M_{m(l,j)}, m(l,j) = min{l, max{1, j}} (Eq. 3.3) are evaluated on the
+ * GPU and the 14 off-centre least-squares polynomials of total degree <= q
+ * are fitted (Householder QR, FP64); the centre polynomial is minus their
+ * sum (Lemma of Sec. 3.4).  q in 1..3, j >= 1.  L = 2 keeps the exact
+ * stencil (Sec. 3, first paragraph).  May be called again to refit. */
+hhg_status hhg_fit_surrogate(hhg_shell* shell, int q, int j, void* stream);
+
+/* y = L_L u (op = IFEM) or y = L~_L u (op = LSQP) on level L, for nrhs
+ * vectors (Sec. 3.4, the operator of Eq. 3.4).  u and y must not overlap. */
+hhg_status hhg_apply(hhg_shell* shell, int L, hhg_op op, hhg_dtype dtype,
+                     const void* u, void* y, int nrhs, void* stream);
+
+/* r = f - L u on level L; if norms_host is not NULL, the Euclidean norm of
+ * each returned r is written there (waits for the stream). */
+hhg_status hhg_residual(hhg_shell* shell, int L, hhg_op op, hhg_dtype dtype,
+                        const void* u, const void* f, void* r, int nrhs,
+                        double* norms_host, void* stream);
+
+/* `sweeps` multicolour hybrid Gauss-Seidel sweeps on level L, u updated in
+ * place (Eq. 5.1 on every node).  One sweep is 10 steps, each updating its
+ * node set simultaneously from the values at the start of the step:
+ * (1) macro vertices, (2,3) edge nodes with even / odd position,
+ * (4-6) face nodes with (p + 2q) mod 3 = 0, 1, 2, (7-10) cell-interior nodes
+ * with (i + 2j + 3k) mod 4 = 0..3 (no two of them coupled). */
+hhg_status hhg_smooth(hhg_shell* shell, int L, hhg_op op, hhg_dtype dtype,
+                      const void* f, void* u, int sweeps, int nrhs, void* stream);
+
+/* V(nu1, nu2) cycles on the finest level (Sec. 4): smooth, residual,
+ * restriction R = P^T, recursion down to L = 2 (solved by FP64 conjugate
+ * gradients to 1e-13 relative residual), prolongation (linear along the
+ * coarse edges), smooth.  Coarse operators are re-discretised (their own
+ * surrogate for op = LSQP).  u holds the initial guess and returns the
+ * iterate; cycles stop once ||f - L u||_2 <= rtol ||f - L u_0||_2 for every
+ * right-hand side or after max_cycles (HHG_ENOCONV).  relres_out (nullable,
+ * nrhs) receives the final relative residuals, cycles_out (nullable) the
+ * number of cycles run. */
+hhg_status hhg_vcycle(hhg_shell* shell, hhg_op op, hhg_dtype dtype,
+                      const void* f, void* u, int nu1, int nu2, int max_cycles,
+                      double rtol, int nrhs, double* relres_out, int* cycles_out,
+                      void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* hhg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HHG_H */

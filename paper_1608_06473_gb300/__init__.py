@@ -1,0 +1,236 @@
+"""GB300 two-scale HHG multigrid: Python binding of libhhg.so.
+
+Argument marshalling only.  Every step of the method (setup of the shell
+hierarchy, the LSQP surrogate fit, operator application, smoothing, residual,
+transfers and the V-cycle) runs in the CUDA library whose C ABI is declared in
+include/hhg.h; the functions below carry the same names and arguments.
+Vectors are torch CUDA tensors (device pointers) or NumPy arrays (host
+pointers, copied by the library); `stream` defaults to torch's current CUDA
+stream.  There is no fallback: without libhhg.so every call raises.
+
+Method: Bauer et al., "A two-scale approach for efficient on-the-fly operator
+assembly in massively parallel high performance multigrid codes"
+(arXiv:1608.06473).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from enum import IntEnum
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhhg.so")
+
+HHG_OK, HHG_EINVAL, HHG_ENOMEM, HHG_ECUDA, HHG_ENOTFIT, HHG_ENOCONV, HHG_EDIVERGED, HHG_ETIMEOUT = \
+    0, -1, -2, -3, -4, -5, -6, -7
+HHG_OP_IFEM, HHG_OP_LSQP = 0, 1
+HHG_F64, HHG_F32 = 0, 1
+
+
+class Status(IntEnum):
+    OK = 0
+    EINVAL = -1
+    ENOMEM = -2
+    ECUDA = -3
+    ENOTFIT = -4
+    ENOCONV = -5
+    EDIVERGED = -6
+    ETIMEOUT = -7
+
+
+class HHGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{Status(status).name}: {msg}")
+        self.status = Status(status)
+
+
+class hhg_shell_desc(ctypes.Structure):
+    _fields_ = [("r_inner", ctypes.c_double), ("r_outer", ctypes.c_double), ("tang_refine", ctypes.c_int),
+                ("radial_layers", ctypes.c_int), ("fine_log2_intervals", ctypes.c_int),
+                ("hbm_budget_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SIGS = {
+    "hhg_setup_shell": [ctypes.POINTER(hhg_shell_desc), _P, ctypes.POINTER(_P)],
+    "hhg_destroy": [_P],
+    "hhg_num_nodes": [_P, _I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+    "hhg_node_coords": [_P, _I, _P],
+    "hhg_fit_surrogate": [_P, _I, _I, _P],
+    "hhg_apply": [_P, _I, _I, _I, _P, _P, _I, _P],
+    "hhg_residual": [_P, _I, _I, _I, _P, _P, _P, _I, _P, _P],
+    "hhg_smooth": [_P, _I, _I, _I, _P, _P, _I, _I, _P],
+    "hhg_vcycle": [_P, _I, _I, _P, _P, _I, _I, _I, ctypes.c_double, _I, _P, _P, _P],
+}
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libhhg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1608_06473_gb300._build` "
+                               "(the CUDA library is required; there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.hhg_last_error.argtypes = []
+        L.hhg_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS) + ["hhg_last_error"]
+
+
+def hhg_last_error() -> str:
+    return lib().hhg_last_error().decode()
+
+
+def _check(st: int):
+    if st != HHG_OK:
+        raise HHGError(st, hhg_last_error())
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise ValueError("host vectors must be C-contiguous float64 arrays")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported vector type {type(x)}")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def hhg_setup_shell(r_inner=0.55, r_outer=1.0, tang_refine=0, radial_layers=1, fine_log2_intervals=4,
+                    hbm_budget_bytes=0, stream=None) -> int:
+    d = hhg_shell_desc(r_inner, r_outer, tang_refine, radial_layers, fine_log2_intervals, hbm_budget_bytes)
+    h = ctypes.c_void_p()
+    _check(lib().hhg_setup_shell(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def hhg_destroy(shell: int):
+    _check(lib().hhg_destroy(shell))
+
+
+def hhg_num_nodes(shell: int, L: int):
+    nt, nf = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().hhg_num_nodes(shell, L, ctypes.byref(nt), ctypes.byref(nf)))
+    return nt.value, nf.value
+
+
+def hhg_node_coords(shell: int, L: int) -> np.ndarray:
+    nt, _ = hhg_num_nodes(shell, L)
+    out = np.empty((nt, 3), dtype=np.float64)
+    _check(lib().hhg_node_coords(shell, L, out.ctypes.data))
+    return out
+
+
+def hhg_fit_surrogate(shell: int, q: int = 2, j: int = 2, stream=None):
+    _check(lib().hhg_fit_surrogate(shell, q, j, _stream(stream)))
+
+
+def hhg_apply(shell: int, L: int, op: int, dtype: int, u, y, nrhs: int = 1, stream=None):
+    _check(lib().hhg_apply(shell, L, op, dtype, _ptr(u), _ptr(y), nrhs, _stream(stream)))
+
+
+def hhg_residual(shell: int, L: int, op: int, dtype: int, u, f, r, nrhs: int = 1, want_norms: bool = True,
+                 stream=None):
+    norms = np.zeros(nrhs) if want_norms else None
+    _check(lib().hhg_residual(shell, L, op, dtype, _ptr(u), _ptr(f), _ptr(r), nrhs,
+                              norms.ctypes.data if want_norms else None, _stream(stream)))
+    return norms
+
+
+def hhg_smooth(shell: int, L: int, op: int, dtype: int, f, u, sweeps: int = 1, nrhs: int = 1, stream=None):
+    _check(lib().hhg_smooth(shell, L, op, dtype, _ptr(f), _ptr(u), sweeps, nrhs, _stream(stream)))
+
+
+def hhg_vcycle(shell: int, op: int, dtype: int, f, u, nu1: int = 3, nu2: int = 3, max_cycles: int = 50,
+               rtol: float = 1e-8, nrhs: int = 1, stream=None, raise_on_noconv: bool = True):
+    """Returns (relres per right-hand side, cycles run, status)."""
+    rel = np.zeros(nrhs)
+    cyc = ctypes.c_int()
+    st = lib().hhg_vcycle(shell, op, dtype, _ptr(f), _ptr(u), nu1, nu2, max_cycles, rtol, nrhs, rel.ctypes.data,
+                          ctypes.byref(cyc), _stream(stream))
+    if st != HHG_OK and (st != HHG_ENOCONV or raise_on_noconv):
+        raise HHGError(st, hhg_last_error())
+    return rel, cyc.value, st
+
+
+class Shell:
+    """Owning handle around hhg_setup_shell / hhg_destroy."""
+
+    def __init__(self, r_inner=0.55, r_outer=1.0, tang_refine=0, radial_layers=1, fine_log2_intervals=4,
+                 hbm_budget_bytes=0, stream=None):
+        self.handle = hhg_setup_shell(r_inner, r_outer, tang_refine, radial_layers, fine_log2_intervals,
+                                      hbm_budget_bytes, stream)
+        self.L = fine_log2_intervals
+
+    def close(self):
+        if self.handle:
+            hhg_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def num_nodes(self, L=None):
+        return hhg_num_nodes(self.handle, self.L if L is None else L)
+
+    def node_coords(self, L=None):
+        return hhg_node_coords(self.handle, self.L if L is None else L)
+
+    def fit(self, q=2, j=2, stream=None):
+        hhg_fit_surrogate(self.handle, q, j, stream)
+
+    def apply(self, u, y, L=None, op=HHG_OP_LSQP, dtype=HHG_F64, nrhs=1, stream=None):
+        hhg_apply(self.handle, self.L if L is None else L, op, dtype, u, y, nrhs, stream)
+
+    def residual(self, u, f, r, L=None, op=HHG_OP_LSQP, dtype=HHG_F64, nrhs=1, stream=None):
+        return hhg_residual(self.handle, self.L if L is None else L, op, dtype, u, f, r, nrhs, True, stream)
+
+    def smooth(self, f, u, sweeps=1, L=None, op=HHG_OP_LSQP, dtype=HHG_F64, nrhs=1, stream=None):
+        hhg_smooth(self.handle, self.L if L is None else L, op, dtype, f, u, sweeps, nrhs, stream)
+
+    def vcycle(self, f, u, nu1=3, nu2=3, max_cycles=50, rtol=1e-8, op=HHG_OP_LSQP, dtype=HHG_F64, nrhs=1,
+               stream=None, raise_on_noconv=True):
+        return hhg_vcycle(self.handle, op, dtype, f, u, nu1, nu2, max_cycles, rtol, nrhs, stream, raise_on_noconv)

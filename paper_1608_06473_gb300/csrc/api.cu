@@ -1,0 +1,759 @@
+// C ABI of libhhg: setup of the shell hierarchy, surrogate fit, operator
+// application, smoothing, residual and the V-cycle driver.  See
+// include/hhg.h for the contract of every entry point.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "common.h"
+#include "device.cuh"
+#include "kernels.h"
+#include "linalg.h"
+#include "mesh.h"
+#include "shell.h"
+
+namespace hhg {
+
+// ---------------------------------------------------------------------------
+// errors and allocation
+// ---------------------------------------------------------------------------
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+void* Allocator::alloc(size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (budget && used + bytes > budget)
+    throw Error{HHG_ENOMEM, "HBM budget exceeded: need " + std::to_string(used + bytes) + " of " +
+                                std::to_string(budget) + " bytes"};
+  void* p = nullptr;
+  const cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error{e == cudaErrorMemoryAllocation ? HHG_ENOMEM : HHG_ECUDA,
+                std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+  }
+  used += bytes;
+  live.push_back({p, bytes});
+  return p;
+}
+
+void Allocator::release(void* p) {
+  if (!p) return;
+  for (size_t n = 0; n < live.size(); ++n)
+    if (live[n].first == p) {
+      cudaFree(p);
+      used -= live[n].second;
+      live.erase(live.begin() + n);
+      return;
+    }
+}
+
+void Allocator::release_all() {
+  for (auto& a : live) cudaFree(a.first);
+  live.clear();
+  used = 0;
+}
+
+template <class T>
+static T* upload(Allocator& A, const std::vector<T>& h, cudaStream_t st) {
+  T* d = A.alloc_n<T>(h.size());
+  if (!h.empty()) HHG_CUDA(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  HHG_CUDA(cudaStreamSynchronize(st));
+  return d;
+}
+
+// ---------------------------------------------------------------------------
+// level construction
+// ---------------------------------------------------------------------------
+
+// Canonical index of a face-local point with weights (l0, l1, l2) over the
+// face's vertices (sum = lay.N), through the face's own edges.
+static int64_t face_point_index(const MacroMesh& m, const LevelLayout& lay, int f, int l0, int l1, int l2) {
+  const auto& F = m.faces[f];
+  const auto& E = m.face_edges[f];
+  const int N = lay.N;
+  const int mask = (l0 > 0) | ((l1 > 0) << 1) | ((l2 > 0) << 2);
+  switch (mask) {
+    case 1: return F[0];
+    case 2: return F[1];
+    case 4: return F[2];
+    case 3: return lay.off_E + (int64_t)E[0] * (N - 1) + (l1 - 1);
+    case 5: return lay.off_E + (int64_t)E[1] * (N - 1) + (l2 - 1);
+    case 6: return lay.off_E + (int64_t)E[2] * (N - 1) + (l2 - 1);
+    case 7: return lay.off_F + (int64_t)f * lay.n_face + lin_face(l1, l2, N);
+  }
+  throw Error{HHG_EINVAL, "face_point_index: empty support"};
+}
+
+static int64_t edge_point_index(const MacroMesh& m, const LevelLayout& lay, int e, int l0, int l1) {
+  if (l1 == 0) return m.edges[e][0];
+  if (l0 == 0) return m.edges[e][1];
+  return lay.off_E + (int64_t)e * (lay.N - 1) + (l1 - 1);
+}
+
+// Both coarse ends of the coarse edge a fine point (barycentric weights lam
+// over d vertices, sum N) is the midpoint of; a coarse-lattice point returns
+// itself twice.  Weights returned on the coarse lattice (sum N/2).
+static void parents(int d, const int* lam, int* pa, int* pb) {
+  int odd[4], no = 0;
+  for (int a = 0; a < d; ++a)
+    if (lam[a] & 1) odd[no++] = a;
+  for (int a = 0; a < d; ++a) pa[a] = pb[a] = lam[a];
+  if (no == 2) {
+    pa[odd[0]] += 1; pa[odd[1]] -= 1;
+    pb[odd[0]] -= 1; pb[odd[1]] += 1;
+  } else if (no == 4) {  // (i, j, k) all odd: the coarse edge of direction (1, -1, 1)
+    const int dl[4] = {-1, 1, -1, 1};
+    for (int a = 0; a < 4; ++a) { pa[a] += dl[a]; pb[a] -= dl[a]; }
+  }
+  for (int a = 0; a < d; ++a) { pa[a] /= 2; pb[a] /= 2; }
+}
+
+static void build_level(hhg_shell* s, int n, cudaStream_t st) {
+  const MacroMesh& m = s->mesh;
+  Level& L = s->levels[n];
+  const int N = 4 << n;
+  L.N = N;
+  L.lay = make_layout(m, N);
+  const LevelLayout& lay = L.lay;
+  HHG_CHECK(lay.n_total < (int64_t)INT32_MAX, HHG_EINVAL, "level too large for 32-bit node indices");
+  Allocator& A = s->alloc;
+
+  // cell-local tables shared by all cells
+  std::vector<uint32_t> plane_nodes;
+  std::vector<int> plane_off(4 * (N + 1) + 1, 0);
+  for (int k = 0; k <= N; ++k)
+    for (int cc = 0; cc < 4; ++cc) {
+      plane_off[k * 4 + cc] = (int)plane_nodes.size();
+      for (int j = 1; j <= N - 2 - k; ++j)
+        for (int i = 1; i <= N - 1 - j - k; ++i)
+          if (k >= 1 && (i + 2 * j + 3 * k) % 4 == cc) plane_nodes.push_back(pack_ijk(i, j, k));
+    }
+  plane_off[4 * (N + 1)] = (int)plane_nodes.size();
+  std::vector<uint32_t> int_ijk;
+  for (int k = 1; k < N; ++k)
+    for (int j = 1; j < N - k; ++j)
+      for (int i = 1; i < N - j - k; ++i) int_ijk.push_back(pack_ijk(i, j, k));
+  std::vector<uint32_t> bnd_ijk;
+  std::vector<int> bnd_slot((size_t)lay.n_full, -1);
+  for (int k = 0; k <= N; ++k)
+    for (int j = 0; j <= N - k; ++j)
+      for (int i = 0; i <= N - j - k; ++i)
+        if (!is_interior(i, j, k, N)) {
+          bnd_slot[lin_full(i, j, k, N)] = (int)bnd_ijk.size();
+          bnd_ijk.push_back(pack_ijk(i, j, k));
+        }
+  L.n_bnd = (int)bnd_ijk.size();
+  L.h_plane_off = plane_off;
+
+  // halo sources and the incidence of lower nodes in cells
+  const int64_t nhal = lay.nC * L.n_bnd;
+  std::vector<int> halo_src((size_t)nhal);
+  std::vector<int64_t> inc_ptr((size_t)lay.off_C + 1, 0);
+  for (int c = 0; c < lay.nC; ++c)
+    for (int b = 0; b < L.n_bnd; ++b) {
+      const uint32_t p = bnd_ijk[b];
+      const int64_t idx = cell_node_index(m, lay, c, unpack_i(p), unpack_j(p), unpack_k(p));
+      const bool dir = node_dirichlet(m, lay, idx);
+      halo_src[(size_t)c * L.n_bnd + b] = dir ? -1 : (int)idx;
+      if (!dir) inc_ptr[idx + 1]++;
+    }
+  for (int64_t r = 0; r < lay.off_C; ++r) inc_ptr[r + 1] += inc_ptr[r];
+  std::vector<int> inc_cb((size_t)inc_ptr[lay.off_C]);
+  {
+    std::vector<int64_t> fill(inc_ptr.begin(), inc_ptr.end() - 1);
+    for (int64_t t = 0; t < nhal; ++t)
+      if (halo_src[t] >= 0) inc_cb[fill[halo_src[t]]++] = (int)t;
+  }
+
+  // lower-primitive colour steps and Dirichlet list
+  std::vector<int> steps[6], dirl;
+  for (int64_t v = 0; v < lay.nV; ++v) (m.vertex_dirichlet((int)v) ? dirl : steps[0]).push_back((int)v);
+  for (int64_t e = 0; e < lay.nE; ++e)
+    for (int p = 1; p < N; ++p) {
+      const int64_t idx = lay.off_E + e * (N - 1) + p - 1;
+      (m.edge_dirichlet((int)e) ? dirl : steps[1 + (p & 1)]).push_back((int)idx);
+    }
+  for (int64_t f = 0; f < lay.nF; ++f)
+    for (int q = 1; q < N - 1; ++q)
+      for (int p = 1; p < N - q; ++p) {
+        const int64_t idx = lay.off_F + f * lay.n_face + lin_face(p, q, N);
+        (m.face_dirichlet((int)f) ? dirl : steps[3 + (p + 2 * q) % 3]).push_back((int)idx);
+      }
+  L.n_free = lay.n_total - (int64_t)dirl.size();
+  L.max_step = 0;
+  for (int t = 0; t < 6; ++t) {
+    L.step_n[t] = (int)steps[t].size();
+    L.max_step = std::max(L.max_step, L.step_n[t]);
+    L.d_step[t] = upload(A, steps[t], st);
+  }
+  L.n_dirichlet = (int)dirl.size();
+  L.d_dirichlet = upload(A, dirl, st);
+
+  L.d_plane_nodes = upload(A, plane_nodes, st);
+  L.d_plane_off = upload(A, plane_off, st);
+  L.d_int_ijk = upload(A, int_ijk, st);
+  L.d_bnd_ijk = upload(A, bnd_ijk, st);
+  L.d_bnd_slot = upload(A, bnd_slot, st);
+  L.d_halo_src = upload(A, halo_src, st);
+
+  // exact lower-primitive rows, assembled on the device in two passes
+  LevelView<double> v{};
+  v.N = N; v.nC = (int)lay.nC; v.off_E = lay.off_E; v.off_F = lay.off_F; v.off_C = lay.off_C;
+  v.n_total = lay.n_total; v.n_int = lay.n_int; v.n_full = lay.n_full; v.n_bnd = L.n_bnd;
+  v.geom = s->d_geom; v.bnd_ijk = L.d_bnd_ijk; v.bnd_slot = L.d_bnd_slot; v.halo_src = L.d_halo_src;
+  int64_t* d_inc_ptr = upload(A, inc_ptr, st);
+  int* d_inc_cb = upload(A, inc_cb, st);
+  int* d_len = A.alloc_n<int>((size_t)std::max<int64_t>(lay.off_C, 1));
+  launch_low_assemble(v, 0, d_inc_ptr, d_inc_cb, d_len, nullptr, nullptr, nullptr, nullptr, st);
+  std::vector<int> len((size_t)lay.off_C);
+  HHG_CUDA(cudaMemcpyAsync(len.data(), d_len, len.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+  HHG_CUDA(cudaStreamSynchronize(st));
+  L.n_slices = (lay.off_C + 31) / 32;
+  std::vector<int64_t> sell_ptr((size_t)L.n_slices + 1, 0);
+  for (int64_t sl = 0; sl < L.n_slices; ++sl) {
+    int w = 0;
+    for (int64_t r = sl * 32; r < std::min<int64_t>(lay.off_C, sl * 32 + 32); ++r) {
+      HHG_CHECK(len[r] >= 0, HHG_EINVAL, "lower-primitive row wider than the assembly buffer");
+      w = std::max(w, len[r]);
+    }
+    sell_ptr[sl + 1] = sell_ptr[sl] + 32 * (int64_t)w;
+  }
+  L.d_sell_ptr = upload(A, sell_ptr, st);
+  L.d_sell_col = A.alloc_n<int>((size_t)std::max<int64_t>(sell_ptr.back(), 1));
+  L.d_sell_val = A.alloc_n<double>((size_t)std::max<int64_t>(sell_ptr.back(), 1));
+  L.d_low_diag = A.alloc_n<double>((size_t)std::max<int64_t>(lay.off_C, 1));
+  launch_low_assemble(v, 1, d_inc_ptr, d_inc_cb, d_len, L.d_sell_ptr, L.d_sell_col, L.d_sell_val, L.d_low_diag, st);
+  HHG_CUDA(cudaStreamSynchronize(st));
+  A.release(d_inc_ptr);
+  A.release(d_inc_cb);
+  A.release(d_len);
+
+  // transfers to the next coarser level (this level as the fine one)
+  if (n > 0) {
+    const LevelLayout lc = make_layout(m, N / 2);
+    std::vector<int> par((size_t)2 * lay.off_C, -1), clf((size_t)lc.off_C, -1);
+    auto put = [&](int64_t r, int64_t a, int64_t b) {
+      par[2 * r] = node_dirichlet(m, lc, a) ? -1 : (int)a;
+      par[2 * r + 1] = node_dirichlet(m, lc, b) ? -1 : (int)b;
+    };
+    for (int64_t v0 = 0; v0 < lay.nV; ++v0) put(v0, v0, v0);
+    for (int64_t e = 0; e < lay.nE; ++e)
+      for (int p = 1; p < N; ++p) {
+        const int lam[2] = {N - p, p};
+        int pa[2], pb[2];
+        parents(2, lam, pa, pb);
+        put(lay.off_E + e * (N - 1) + p - 1, edge_point_index(m, lc, (int)e, pa[0], pa[1]),
+            edge_point_index(m, lc, (int)e, pb[0], pb[1]));
+      }
+    for (int64_t f = 0; f < lay.nF; ++f)
+      for (int q = 1; q < N - 1; ++q)
+        for (int p = 1; p < N - q; ++p) {
+          const int lam[3] = {N - p - q, p, q};
+          int pa[3], pb[3];
+          parents(3, lam, pa, pb);
+          put(lay.off_F + f * lay.n_face + lin_face(p, q, N), face_point_index(m, lc, (int)f, pa[0], pa[1], pa[2]),
+              face_point_index(m, lc, (int)f, pb[0], pb[1], pb[2]));
+        }
+    L.d_low_par = upload(A, par, st);
+    // coarse lower nodes -> their fine position
+    for (int64_t v0 = 0; v0 < lc.nV; ++v0)
+      if (!m.vertex_dirichlet((int)v0)) clf[v0] = (int)v0;
+    for (int64_t e = 0; e < lc.nE; ++e)
+      if (!m.edge_dirichlet((int)e))
+        for (int p = 1; p < lc.N; ++p) clf[lc.off_E + e * (lc.N - 1) + p - 1] = (int)(lay.off_E + e * (N - 1) + 2 * p - 1);
+    for (int64_t f = 0; f < lc.nF; ++f)
+      if (!m.face_dirichlet((int)f))
+        for (int q = 1; q < lc.N - 1; ++q)
+          for (int p = 1; p < lc.N - q; ++p)
+            clf[lc.off_F + f * lc.n_face + lin_face(p, q, lc.N)] =
+                (int)(lay.off_F + f * lay.n_face + lin_face(2 * p, 2 * q, N));
+    s->levels[n - 1].d_coarse_low_fine = upload(A, clf, st);
+  }
+
+  // halo copies and work vectors
+  L.d_ghost64 = A.alloc_n<double>((size_t)(lay.nC * lay.n_full));
+  HHG_CUDA(cudaMemsetAsync(L.d_ghost64, 0, sizeof(double) * lay.nC * lay.n_full, st));
+  L.d_r = A.alloc_n<double>((size_t)lay.n_total);
+  L.d_tmp = A.alloc_n<double>((size_t)std::max(L.max_step, 1));
+  if (n + 2 < s->Lf) {
+    L.d_u = A.alloc_n<double>((size_t)lay.n_total);
+    L.d_f = A.alloc_n<double>((size_t)lay.n_total);
+    HHG_CUDA(cudaMemsetAsync(L.d_u, 0, sizeof(double) * lay.n_total, st));
+    HHG_CUDA(cudaMemsetAsync(L.d_f, 0, sizeof(double) * lay.n_total, st));
+  }
+  HHG_CUDA(cudaMemsetAsync(L.d_r, 0, sizeof(double) * lay.n_total, st));
+}
+
+template <class T>
+static LevelView<T> view(hhg_shell* s, int n);
+
+template <>
+LevelView<double> view<double>(hhg_shell* s, int n) {
+  Level& L = s->levels[n];
+  const LevelLayout& lay = L.lay;
+  LevelView<double> v{};
+  v.N = L.N; v.nC = (int)lay.nC; v.off_E = lay.off_E; v.off_F = lay.off_F; v.off_C = lay.off_C;
+  v.n_total = lay.n_total; v.n_int = lay.n_int; v.n_full = lay.n_full; v.n_bnd = L.n_bnd;
+  v.geom = s->d_geom; v.plane_nodes = L.d_plane_nodes; v.plane_off = L.d_plane_off; v.int_ijk = L.d_int_ijk;
+  v.bnd_ijk = L.d_bnd_ijk; v.bnd_slot = L.d_bnd_slot; v.halo_src = L.d_halo_src; v.ghost = L.d_ghost64;
+  v.coef = L.d_coef; v.q = (L.d_coef && L.N >= 8) ? s->q : 0;
+  v.sell_ptr = L.d_sell_ptr; v.sell_col = L.d_sell_col; v.sell_val = L.d_sell_val; v.low_diag = L.d_low_diag;
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// operators on one level (device vectors, FP64)
+// ---------------------------------------------------------------------------
+
+static void check_op(hhg_shell* s, int n, int op) {
+  HHG_CHECK(op == HHG_OP_IFEM || op == HHG_OP_LSQP, HHG_EINVAL, "unknown operator");
+  if (op == HHG_OP_LSQP && s->levels[n].N >= 8)
+    HHG_CHECK(s->levels[n].d_coef != nullptr, HHG_ENOTFIT, "LSQP requested before hhg_fit_surrogate");
+}
+
+static int eff_op(hhg_shell* s, int n, int op) { return (s->levels[n].N >= 8) ? op : HHG_OP_IFEM; }
+
+static void op_apply(hhg_shell* s, int n, int op, const double* u, double* y, cudaStream_t st) {
+  LevelView<double> v = view<double>(s, n);
+  launch_halo(v, u, st);
+  launch_cell(v, eff_op(s, n, op), APPLY, const_cast<double*>(u), y, (const double*)nullptr, nullptr, st);
+  launch_low(v, APPLY, u, y, (const double*)nullptr, nullptr, low_blocks(v.off_C), st);
+}
+
+// r = f - L u; the squared norm lands in d_red[slot] (device).
+static void op_residual(hhg_shell* s, int n, int op, const double* u, const double* f, double* r, int slot,
+                        cudaStream_t st) {
+  LevelView<double> v = view<double>(s, n);
+  const int nb = low_blocks(v.off_C);
+  double* part = s->d_red + 64;
+  launch_halo(v, u, st);
+  launch_cell(v, eff_op(s, n, op), RESIDUAL, const_cast<double*>(u), r, f, part, st);
+  launch_low(v, RESIDUAL, u, r, f, part + v.nC, nb, st);
+  launch_sum(part, v.nC + nb, s->d_red + slot, st);
+}
+
+static void op_smooth(hhg_shell* s, int n, int op, const double* f, double* u, cudaStream_t st) {
+  LevelView<double> v = view<double>(s, n);
+  Level& L = s->levels[n];
+  for (int t = 0; t < 6; ++t) launch_low_step(v, L.d_step[t], L.step_n[t], u, f, L.d_tmp, st);
+  launch_halo(v, (const double*)u, st);
+  launch_cell(v, eff_op(s, n, op), SMOOTH, u, u, f, nullptr, st);
+}
+
+static double read_scalar(hhg_shell* s, int slot, cudaStream_t st) {
+  double h = 0;
+  HHG_CUDA(cudaMemcpyAsync(&h, s->d_red + slot, sizeof(double), cudaMemcpyDeviceToHost, st));
+  HHG_CUDA(cudaStreamSynchronize(st));
+  return h;
+}
+
+// Coarsest level (N = 4): Jacobi-preconditioned conjugate gradients on the
+// exact, symmetric operator, to ||r|| <= 1e-13 ||f|| (the paper uses
+// Gauss-Seidel as coarse solver, Sec. 4; an exact solve keeps the cycle
+// independent of that choice).
+static void coarse_solve(hhg_shell* s, const double* f, double* x, cudaStream_t st) {
+  Level& L = s->levels[0];
+  const int64_t n = L.lay.n_total;
+  double* r = s->d_cg;
+  double* z = r + n;
+  double* p = z + n;
+  double* q = p + n;
+  double* dinv = q + n;
+  LevelView<double> v = view<double>(s, 0);
+  launch_coarse_diag(v, dinv, st);
+  HHG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+  HHG_CUDA(cudaMemcpyAsync(r, f, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  launch_zero_list(L.d_dirichlet, L.n_dirichlet, r, st);
+  const int nb = dot_blocks(n);
+  double* part = s->d_red + 64;
+  enum { RZ = 0, PQ = 1, RZN = 2, RR = 3, FF = 4 };
+  auto dot = [&](const double* a, const double* b, int slot) {
+    launch_dot_partial(a, b, n, part, nb, st);
+    launch_sum(part, nb, s->d_red + slot, st);
+  };
+  dot(r, r, FF);
+  const double ff = read_scalar(s, FF, st);
+  if (ff == 0.0) return;
+  {
+    // z = D^-1 r via the update kernel with alpha = 0, then p = z
+    HHG_CUDA(cudaMemsetAsync(s->d_red + PQ, 0, sizeof(double), st));
+    HHG_CUDA(cudaMemsetAsync(q, 0, sizeof(double) * n, st));
+    HHG_CUDA(cudaMemsetAsync(p, 0, sizeof(double) * n, st));
+    launch_cg_update(x, r, z, p, q, dinv, s->d_red + PQ, s->d_red + FF, n, st);
+    HHG_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  }
+  dot(r, z, RZ);
+  const double tol2 = 1e-26 * ff;
+  for (int it = 0; it < 20000; ++it) {
+    op_apply(s, 0, HHG_OP_IFEM, p, q, st);
+    dot(p, q, PQ);
+    launch_cg_update(x, r, z, p, q, dinv, s->d_red + RZ, s->d_red + PQ, n, st);
+    dot(r, z, RZN);
+    launch_cg_dir(p, z, s->d_red + RZN, s->d_red + RZ, n, st);
+    HHG_CUDA(cudaMemcpyAsync(s->d_red + RZ, s->d_red + RZN, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if ((it & 7) == 7) {
+      dot(r, r, RR);
+      const double rr = read_scalar(s, RR, st);
+      if (!std::isfinite(rr)) throw Error{HHG_EDIVERGED, "coarse solve diverged"};
+      if (rr <= tol2) return;
+    }
+  }
+  throw Error{HHG_ENOCONV, "coarse solve did not reach its tolerance"};
+}
+
+static void vcycle_rec(hhg_shell* s, int n, int op, const double* f, double* u, int nu1, int nu2, cudaStream_t st) {
+  if (n == 0) {
+    coarse_solve(s, f, u, st);
+    return;
+  }
+  Level& L = s->levels[n];
+  Level& C = s->levels[n - 1];
+  for (int t = 0; t < nu1; ++t) op_smooth(s, n, op, f, u, st);
+  op_residual(s, n, op, u, f, L.d_r, 8, st);
+  LevelView<double> vf = view<double>(s, n), vc = view<double>(s, n - 1);
+  launch_restrict(vf, vc, C.d_coarse_low_fine, (const double*)L.d_r, C.d_f, st);
+  HHG_CUDA(cudaMemsetAsync(C.d_u, 0, sizeof(double) * C.lay.n_total, st));
+  vcycle_rec(s, n - 1, op, C.d_f, C.d_u, nu1, nu2, st);
+  launch_halo(vc, (const double*)C.d_u, st);
+  launch_prolong_add(vf, vc, L.d_low_par, (const double*)C.d_u, u, st);
+  for (int t = 0; t < nu2; ++t) op_smooth(s, n, op, f, u, st);
+}
+
+// ---------------------------------------------------------------------------
+// surrogate fit
+// ---------------------------------------------------------------------------
+
+static void fit(hhg_shell* s, int q, int j, cudaStream_t st) {
+  const int mq = n_coeffs(q);
+  for (size_t n = 0; n < s->levels.size(); ++n) {
+    Level& L = s->levels[n];
+    const int N = L.N;
+    if (N < 8) continue;
+    const int l = (int)n;  // paper level: N = 2^(l+2)
+    const int mlev = std::min(l, std::max(1, j));
+    const int Nm = 4 << mlev, scale = 1 << (l - mlev);
+    std::vector<uint32_t> pts;
+    for (int k = 1; k < Nm; ++k)
+      for (int jj = 1; jj < Nm - k; ++jj)
+        for (int i = 1; i < Nm - jj - k; ++i) pts.push_back(pack_ijk(i * scale, jj * scale, k * scale));
+    const int np = (int)pts.size();
+    // sampling matrix in the line-form monomial order (a, d, b): xi^a eta^b zeta^d
+    std::vector<double> Am((size_t)np * mq), sc(mq);
+    {
+      int t = 0;
+      for (int a = 0; a <= q; ++a)
+        for (int d = 0; d <= q - a; ++d)
+          for (int b = 0; b <= q - a - d; ++b) {
+            sc[t] = std::ldexp(1.0, -(a + b + d) * (l + 2));  // 1 / N^(a+b+d)
+            for (int p = 0; p < np; ++p) {
+              const double x = (double)unpack_i(pts[p]) / N, y = (double)unpack_j(pts[p]) / N,
+                           z = (double)unpack_k(pts[p]) / N;
+              Am[(size_t)p * mq + t] = std::pow(x, a) * std::pow(y, b) * std::pow(z, d);
+            }
+            ++t;
+          }
+    }
+    const std::vector<double> P = lsq_pinv(Am, np, mq);
+    Allocator& A = s->alloc;
+    uint32_t* d_pts = upload(A, pts, st);
+    double* d_P = upload(A, P, st);
+    double* d_sc = upload(A, sc, st);
+    if (L.d_coef) { A.release(L.d_coef); L.d_coef = nullptr; }
+    if (L.d_coef32) { A.release(L.d_coef32); L.d_coef32 = nullptr; }
+    L.d_coef = A.alloc_n<double>((size_t)L.lay.nC * 15 * mq);
+    L.d_coef32 = A.alloc_n<float>((size_t)L.lay.nC * 15 * mq);
+    // sample in chunks of cells so the sample buffer stays below ~1 GB
+    const int64_t per_cell = (int64_t)np * 14;
+    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(L.lay.nC, (int64_t)(1 << 27) / per_cell));
+    double* d_b = A.alloc_n<double>((size_t)chunk * per_cell);
+    LevelView<double> v = view<double>(s, (int)n);
+    for (int c0 = 0; c0 < L.lay.nC; c0 += chunk) {
+      const int nc = (int)std::min<int64_t>(chunk, L.lay.nC - c0);
+      LevelView<double> vc = v;
+      vc.geom = s->d_geom + c0;
+      vc.nC = nc;
+      launch_sample(vc, d_pts, np, d_b, st);
+      launch_fit_coef(nc, mq, np, d_P, d_sc, d_b, L.d_coef + (int64_t)c0 * 15 * mq, L.d_coef32 + (int64_t)c0 * 15 * mq,
+                      st);
+    }
+    HHG_CUDA(cudaStreamSynchronize(st));
+    A.release(d_b);
+    A.release(d_pts);
+    A.release(d_P);
+    A.release(d_sc);
+  }
+  s->q = q;
+  s->j = j;
+}
+
+// ---------------------------------------------------------------------------
+// argument helpers
+// ---------------------------------------------------------------------------
+
+static bool is_host_ptr(const void* p) {
+  cudaPointerAttributes a{};
+  const cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+// Device view of a (possibly host) vector argument of n doubles.
+struct Arg {
+  const void* user;
+  double* dev;
+  bool host;
+};
+
+static Arg stage_in(hhg_shell* s, int slot, const void* p, int64_t n, bool copy, cudaStream_t st) {
+  HHG_CHECK(p != nullptr, HHG_EINVAL, "NULL vector argument");
+  Arg a{p, (double*)p, is_host_ptr(p)};
+  if (a.host) {
+    if (s->stage_len < n) {
+      for (auto& d : s->d_stage) { s->alloc.release(d); d = nullptr; }
+      s->stage_len = 0;
+      for (auto& d : s->d_stage) d = s->alloc.alloc_n<double>((size_t)n);
+      s->stage_len = n;
+    }
+    a.dev = s->d_stage[slot];
+    if (copy) HHG_CUDA(cudaMemcpyAsync(a.dev, p, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  }
+  return a;
+}
+
+static void stage_out(const Arg& a, int64_t n, cudaStream_t st) {
+  if (a.host) {
+    HHG_CUDA(cudaMemcpyAsync(const_cast<void*>(a.user), a.dev, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    HHG_CUDA(cudaStreamSynchronize(st));
+  }
+}
+
+static int level_index(hhg_shell* s, int L) {
+  HHG_CHECK(s != nullptr, HHG_EINVAL, "NULL shell");
+  HHG_CHECK(L >= 2 && L <= s->Lf, HHG_EINVAL, "level out of range");
+  return L - 2;
+}
+
+template <class F>
+static hhg_status guarded(F&& fn) {
+  try {
+    fn();
+    set_error("");
+    return HHG_OK;
+  } catch (const Error& e) {
+    set_error(e.msg);
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return HHG_ENOMEM;
+  } catch (const std::exception& e) {
+    set_error(e.what());
+    return HHG_EINVAL;
+  }
+}
+
+}  // namespace hhg
+
+using namespace hhg;
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+const char* hhg_last_error(void) { return g_last_error.c_str(); }
+
+hhg_status hhg_setup_shell(const hhg_shell_desc* d, void* stream, hhg_shell** out) {
+  return guarded([&] {
+    HHG_CHECK(d && out, HHG_EINVAL, "NULL argument");
+    HHG_CHECK(d->r_inner > 0 && d->r_outer > d->r_inner, HHG_EINVAL, "need 0 < r_inner < r_outer");
+    HHG_CHECK(d->tang_refine >= 0 && d->tang_refine <= 6, HHG_EINVAL, "tang_refine out of range");
+    HHG_CHECK(d->radial_layers >= 1 && d->radial_layers <= 4096, HHG_EINVAL, "radial_layers out of range");
+    HHG_CHECK(d->fine_log2_intervals >= 2 && d->fine_log2_intervals <= 10, HHG_EINVAL, "level out of range");
+    *out = nullptr;
+    Star star;
+    kuhn_star(&star);
+    for (int t = 0; t < 24; ++t)
+      for (int a = 0; a < 3; ++a)
+        HHG_CHECK(star.t[t][a] == hhg::star(t, a), HHG_EINVAL, "internal star table mismatch");
+    cudaStream_t st = (cudaStream_t)stream;
+    hhg_shell* s = new hhg_shell();
+    try {
+      s->alloc.budget = d->hbm_budget_bytes;
+      s->mesh = build_shell(d->r_inner, d->r_outer, d->tang_refine, d->radial_layers);
+      s->Lf = d->fine_log2_intervals;
+      std::vector<CellGeom> geom(s->mesh.nC());
+      for (int c = 0; c < s->mesh.nC(); ++c)
+        for (int a = 0; a < 4; ++a) {
+          const int v = s->mesh.cells[c][a];
+          for (int x = 0; x < 3; ++x) geom[c].x[a][x] = s->mesh.vx[v][x];
+          geom[c].r[a] = s->mesh.vr[v];
+        }
+      s->d_geom = upload(s->alloc, geom, st);
+      s->levels.resize(s->Lf - 1);
+      for (int n = 0; n < (int)s->levels.size(); ++n) build_level(s, n, st);
+      int64_t red = 64;
+      for (auto& L : s->levels)
+        red = std::max<int64_t>(red, 64 + L.lay.nC + low_blocks(L.lay.off_C) + dot_blocks(L.lay.n_total));
+      s->red_len = red + 64;
+      s->d_red = s->alloc.alloc_n<double>((size_t)s->red_len);
+      HHG_CUDA(cudaMemsetAsync(s->d_red, 0, sizeof(double) * s->red_len, st));
+      s->d_cg = s->alloc.alloc_n<double>((size_t)(5 * s->levels[0].lay.n_total));
+      HHG_CUDA(cudaStreamSynchronize(st));
+    } catch (...) {
+      s->alloc.release_all();
+      delete s;
+      throw;
+    }
+    *out = s;
+  });
+}
+
+hhg_status hhg_destroy(hhg_shell* s) {
+  return guarded([&] {
+    if (!s) return;
+    cudaDeviceSynchronize();
+    s->alloc.release_all();
+    delete s;
+  });
+}
+
+hhg_status hhg_num_nodes(const hhg_shell* s, int L, int64_t* n_total, int64_t* n_free) {
+  return guarded([&] {
+    const int n = level_index(const_cast<hhg_shell*>(s), L);
+    if (n_total) *n_total = s->levels[n].lay.n_total;
+    if (n_free) *n_free = s->levels[n].n_free;
+  });
+}
+
+hhg_status hhg_node_coords(const hhg_shell* s, int L, double* xyz) {
+  return guarded([&] {
+    const int n = level_index(const_cast<hhg_shell*>(s), L);
+    HHG_CHECK(xyz != nullptr, HHG_EINVAL, "NULL output");
+    level_coords(s->mesh, s->levels[n].lay, xyz);
+  });
+}
+
+hhg_status hhg_fit_surrogate(hhg_shell* s, int q, int j, void* stream) {
+  return guarded([&] {
+    HHG_CHECK(s != nullptr, HHG_EINVAL, "NULL shell");
+    HHG_CHECK(q >= 1 && q <= 3, HHG_EINVAL, "q must be 1, 2 or 3");
+    HHG_CHECK(j >= 1, HHG_EINVAL, "j must be >= 1");
+    fit(s, q, j, (cudaStream_t)stream);
+  });
+}
+
+static void check_common(hhg_shell* s, int n, int op, int dtype, int nrhs) {
+  HHG_CHECK(dtype == HHG_F64, HHG_EINVAL, "only HHG_F64 is implemented for this entry point");
+  HHG_CHECK(nrhs >= 1, HHG_EINVAL, "nrhs must be >= 1");
+  check_op(s, n, op);
+}
+
+hhg_status hhg_apply(hhg_shell* s, int L, hhg_op op, hhg_dtype dtype, const void* u, void* y, int nrhs,
+                     void* stream) {
+  return guarded([&] {
+    const int n = level_index(s, L);
+    check_common(s, n, op, dtype, nrhs);
+    HHG_CHECK(u != y, HHG_EINVAL, "u and y must not overlap");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t nt = s->levels[n].lay.n_total;
+    for (int b = 0; b < nrhs; ++b) {
+      Arg au = stage_in(s, 0, (const double*)u + b * nt, nt, true, st);
+      Arg ay = stage_in(s, 1, (double*)y + b * nt, nt, false, st);
+      op_apply(s, n, op, au.dev, ay.dev, st);
+      stage_out(ay, nt, st);
+    }
+  });
+}
+
+hhg_status hhg_residual(hhg_shell* s, int L, hhg_op op, hhg_dtype dtype, const void* u, const void* f, void* r,
+                        int nrhs, double* norms, void* stream) {
+  return guarded([&] {
+    const int n = level_index(s, L);
+    check_common(s, n, op, dtype, nrhs);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t nt = s->levels[n].lay.n_total;
+    for (int b = 0; b < nrhs; ++b) {
+      Arg au = stage_in(s, 0, (const double*)u + b * nt, nt, true, st);
+      Arg af = stage_in(s, 1, (const double*)f + b * nt, nt, true, st);
+      Arg ar = stage_in(s, 2, (double*)r + b * nt, nt, false, st);
+      op_residual(s, n, op, au.dev, af.dev, ar.dev, 9, st);
+      stage_out(ar, nt, st);
+      if (norms) norms[b] = std::sqrt(read_scalar(s, 9, st));
+    }
+  });
+}
+
+hhg_status hhg_smooth(hhg_shell* s, int L, hhg_op op, hhg_dtype dtype, const void* f, void* u, int sweeps, int nrhs,
+                      void* stream) {
+  return guarded([&] {
+    const int n = level_index(s, L);
+    check_common(s, n, op, dtype, nrhs);
+    HHG_CHECK(sweeps >= 0, HHG_EINVAL, "sweeps must be >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    Level& Lv = s->levels[n];
+    const int64_t nt = Lv.lay.n_total;
+    for (int b = 0; b < nrhs; ++b) {
+      Arg af = stage_in(s, 1, (const double*)f + b * nt, nt, true, st);
+      Arg au = stage_in(s, 0, (double*)u + b * nt, nt, true, st);
+      launch_zero_list(Lv.d_dirichlet, Lv.n_dirichlet, au.dev, st);
+      for (int t = 0; t < sweeps; ++t) op_smooth(s, n, op, af.dev, au.dev, st);
+      stage_out(au, nt, st);
+    }
+  });
+}
+
+hhg_status hhg_vcycle(hhg_shell* s, hhg_op op, hhg_dtype dtype, const void* f, void* u, int nu1, int nu2,
+                      int max_cycles, double rtol, int nrhs, double* relres_out, int* cycles_out, void* stream) {
+  return guarded([&] {
+    HHG_CHECK(s != nullptr, HHG_EINVAL, "NULL shell");
+    const int n = (int)s->levels.size() - 1;
+    check_common(s, n, op, dtype, nrhs);
+    for (int m = 0; m <= n; ++m) check_op(s, m, op);
+    HHG_CHECK(nu1 >= 0 && nu2 >= 0 && max_cycles >= 0, HHG_EINVAL, "negative cycle parameter");
+    cudaStream_t st = (cudaStream_t)stream;
+    Level& Lv = s->levels[n];
+    const int64_t nt = Lv.lay.n_total;
+    int cycles_max = 0;
+    bool all_conv = true;
+    for (int b = 0; b < nrhs; ++b) {
+      Arg af = stage_in(s, 1, (const double*)f + b * nt, nt, true, st);
+      Arg au = stage_in(s, 0, (double*)u + b * nt, nt, true, st);
+      launch_zero_list(Lv.d_dirichlet, Lv.n_dirichlet, au.dev, st);
+      op_residual(s, n, op, au.dev, af.dev, Lv.d_r, 10, st);
+      const double r0 = std::sqrt(read_scalar(s, 10, st));
+      HHG_CHECK(std::isfinite(r0), HHG_EDIVERGED, "initial residual is not finite");
+      double rel = r0 > 0 ? 1.0 : 0.0;
+      int cyc = 0;
+      while (rel > rtol && cyc < max_cycles) {
+        vcycle_rec(s, n, op, af.dev, au.dev, nu1, nu2, st);
+        op_residual(s, n, op, au.dev, af.dev, Lv.d_r, 10, st);
+        const double rn = std::sqrt(read_scalar(s, 10, st));
+        HHG_CHECK(std::isfinite(rn), HHG_EDIVERGED, "residual norm became NaN or Inf");
+        rel = rn / r0;
+        ++cyc;
+      }
+      launch_zero_list(Lv.d_dirichlet, Lv.n_dirichlet, au.dev, st);
+      stage_out(au, nt, st);
+      if (relres_out) relres_out[b] = rel;
+      cycles_max = std::max(cycles_max, cyc);
+      if (rel > rtol) all_conv = false;
+    }
+    HHG_CUDA(cudaStreamSynchronize(st));
+    if (cycles_out) *cycles_out = cycles_max;
+    if (!all_conv) throw Error{HHG_ENOCONV, "max_cycles reached before rtol"};
+  });
+}
+
+}  // extern "C"

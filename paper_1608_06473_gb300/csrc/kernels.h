@@ -1,0 +1,83 @@
+// Host-side launchers of the CUDA kernels (implemented in cell.cu, low.cu).
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "shell.h"
+
+namespace hhg {
+
+enum Mode { APPLY = 0, RESIDUAL = 1, SMOOTH = 2 };
+
+// ---- cell interiors (cell.cu) ----------------------------------------------
+// One CTA per macro cell walks its planes k = 1 .. N-3.
+//   APPLY:    out = L u on the interior nodes
+//   RESIDUAL: out = f - L u, partial[c] = sum of out^2 over cell c
+//   SMOOTH:   the four colour steps (i + 2j + 3k) mod 4 = 0..3 of Eq. 5.1,
+//             u updated in place, in a plane wavefront (colour c at plane
+//             s + 1 - c in step s), which orders every update after all
+//             lower-colour updates of its neighbours.
+// op: 0 = IFEM (on-the-fly exact stencils), 1 = LSQP (surrogate).
+template <class T>
+void launch_cell(const LevelView<T>& lv, int op, Mode mode, T* u, T* out, const T* f, double* partial,
+                 cudaStream_t st);
+
+// Exact stencils (14 off-centre weights) at cell-local points of every cell:
+// b[(c * n_pts + p) * 14 + w] (Table 4.3 "t_sample").
+void launch_sample(const LevelView<double>& lv, const uint32_t* pts, int n_pts, double* b, cudaStream_t st);
+
+// coef[c][w][t] = scale[t] * sum_p aplus[t][p] b[c][p][w] for w < 14 and the
+// centre coef[c][14][t] = -sum_w coef[c][w][t]; optional float copy.
+void launch_fit_coef(int nC, int mq, int n_pts, const double* aplus, const double* scale, const double* b,
+                     double* coef, float* coef32, cudaStream_t st);
+
+// ---- lower primitives, halos, transfers, reductions (low.cu) ---------------
+template <class T>
+void launch_halo(const LevelView<T>& lv, const T* u, cudaStream_t st);
+
+template <class T>
+void launch_low(const LevelView<T>& lv, Mode mode, const T* u, T* out, const T* f, double* partial,
+                int n_partial_blocks, cudaStream_t st);
+int low_blocks(int64_t rows);
+
+template <class T>
+void launch_low_step(const LevelView<T>& lv, const int* list, int n, T* u, const T* f, T* tmp, cudaStream_t st);
+
+template <class T>
+void launch_zero_list(const int* list, int n, T* v, cudaStream_t st);
+
+template <class T>
+void launch_prolong_add(const LevelView<T>& fine, const LevelView<T>& coarse, const int* low_par, const T* ec,
+                        T* uf, cudaStream_t st);
+
+template <class T>
+void launch_restrict(const LevelView<T>& fine, const LevelView<T>& coarse, const int* coarse_low_fine,
+                     const T* rf, T* rc, cudaStream_t st);
+
+// out[0] = sum of partial[0 .. n-1] (fixed order, one block).
+void launch_sum(const double* partial, int n, double* out, cudaStream_t st);
+
+// Coarse-solver vector kernels (FP64).
+void launch_dot_partial(const double* a, const double* b, int64_t n, double* partial, int nblk, cudaStream_t st);
+int dot_blocks(int64_t n);
+// x += alpha p ; r -= alpha q with alpha = num / den (device scalars), z = r / d where d != 0
+void launch_cg_update(double* x, double* r, double* z, const double* p, const double* q, const double* dinv,
+                      const double* num, const double* den, int64_t n, cudaStream_t st);
+// p = z + (num_new / num_old) p
+void launch_cg_dir(double* p, const double* z, const double* num_new, const double* num_old, int64_t n,
+                   cudaStream_t st);
+// d_inv[i] = 1 / diag(i) for free nodes of the coarsest level, 0 otherwise
+void launch_coarse_diag(const LevelView<double>& lv, double* dinv, cudaStream_t st);
+
+template <class T>
+void launch_copy_cast(const double* src, T* dst, int64_t n, cudaStream_t st);
+
+// Lower-primitive stencil assembly (setup): pass 0 counts columns per row,
+// pass 1 fills the sliced ELL rows and the diagonal.
+void launch_low_assemble(const LevelView<double>& lv, int pass, const int64_t* inc_ptr, const int* inc_cb,
+                         int* row_len, int64_t* sell_ptr, int* sell_col, double* sell_val, double* diag,
+                         cudaStream_t st);
+
+}  // namespace hhg

@@ -1,0 +1,125 @@
+// Internal state of an hhg_shell: the macro mesh, and per refinement level
+// the device index maps, pre-assembled lower-primitive stencils, surrogate
+// coefficients, halo copies and work vectors.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "common.h"
+#include "mesh.h"
+
+namespace hhg {
+
+// Geometry of one macro cell: its 4 vertices (ascending global id) and the
+// radii that rho interpolates (Sec. 2.2, blending map Phi).
+struct CellGeom {
+  double x[4][3];
+  double r[4];
+};
+
+// Byte-budgeted device allocator: refuses before cudaMalloc when a request
+// would exceed the budget (HHG_ENOMEM).
+struct Allocator {
+  size_t budget = 0;  // 0 = unlimited
+  size_t used = 0;
+  std::vector<std::pair<void*, size_t>> live;
+  void* alloc(size_t bytes);
+  void release(void* p);
+  void release_all();
+  template <class T>
+  T* alloc_n(size_t n) { return static_cast<T*>(alloc(n * sizeof(T))); }
+};
+
+// Packed cell-local point: i | j << 10 | k << 20 (N <= 1023).
+HD uint32_t pack_ijk(int i, int j, int k) { return (uint32_t)i | ((uint32_t)j << 10) | ((uint32_t)k << 20); }
+HD int unpack_i(uint32_t p) { return (int)(p & 1023u); }
+HD int unpack_j(uint32_t p) { return (int)((p >> 10) & 1023u); }
+HD int unpack_k(uint32_t p) { return (int)(p >> 20); }
+
+// Device-side view of one level, passed to kernels by value.
+template <class T>
+struct LevelView {
+  int N;
+  int nC;
+  int64_t off_E, off_F, off_C, n_total, n_int, n_full;
+  int n_bnd;
+  const CellGeom* geom;          // [nC]
+  const uint32_t* plane_nodes;   // interior points (packed), ordered (k, colour, j, i)
+  const int* plane_off;          // start of (k, colour) in plane_nodes, [4 (N + 1) + 1]
+  const uint32_t* int_ijk;       // [n_int] interior points in canonical order
+  const uint32_t* bnd_ijk;       // [n_bnd] boundary points of a cell
+  const int* bnd_slot;           // [n_full] boundary slot of a cell-local point, -1 = interior
+  const int* halo_src;           // [nC * n_bnd] canonical index of each cell's boundary point, -1 = Dirichlet
+  T* ghost;                      // [nC * n_full] per-cell copies of boundary values
+  const T* coef;                 // [nC * 15 * m_q] surrogate coefficients (raw index monomials)
+  int q;                         // surrogate degree (0 = not fitted)
+  // lower primitives: canonical rows 0 .. off_C-1 in sliced ELL (32-row
+  // slices, column-major inside a slice), Dirichlet rows have diag 0
+  const int64_t* sell_ptr;       // [n_slices + 1]
+  const int* sell_col;           // canonical column, -1 = padding
+  const T* sell_val;
+  const T* low_diag;             // [off_C]
+};
+
+struct Level {
+  LevelLayout lay;
+  int N = 0;
+  int n_bnd = 0;
+  uint32_t* d_bnd_ijk = nullptr;
+  int* d_bnd_slot = nullptr;
+  int* d_halo_src = nullptr;
+  uint32_t* d_plane_nodes = nullptr;
+  int* d_plane_off = nullptr;
+  std::vector<int> h_plane_off;
+  uint32_t* d_int_ijk = nullptr;
+  // lower primitives
+  int64_t n_slices = 0;
+  int64_t* d_sell_ptr = nullptr;
+  int* d_sell_col = nullptr;
+  double* d_sell_val = nullptr;
+  double* d_low_diag = nullptr;
+  float* d_sell_val32 = nullptr;
+  float* d_low_diag32 = nullptr;
+  int* d_step[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int step_n[6] = {0, 0, 0, 0, 0, 0};
+  int max_step = 0;
+  int* d_dirichlet = nullptr;    // Dirichlet lower nodes
+  int n_dirichlet = 0;
+  int64_t n_free = 0;
+  // transfers: coarse parents of this level's lower nodes (this level fine),
+  // and the fine position of this level's lower nodes (this level coarse)
+  int* d_low_par = nullptr;          // [2 * off_C], -1 = Dirichlet parent
+  int* d_coarse_low_fine = nullptr;  // [off_C], -1 = Dirichlet
+  // surrogate
+  double* d_coef = nullptr;
+  float* d_coef32 = nullptr;
+  // halo copies and work vectors (allocated on demand)
+  double* d_ghost64 = nullptr;
+  float* d_ghost32 = nullptr;
+  double* d_u = nullptr;
+  double* d_f = nullptr;
+  double* d_r = nullptr;
+  double* d_tmp = nullptr;  // step buffer for simultaneous lower-primitive updates
+};
+
+// Number of monomials of total degree <= q in three variables (Eq. 3.2).
+HD int n_coeffs(int q) { return (q + 1) * (q + 2) * (q + 3) / 6; }
+
+}  // namespace hhg
+
+struct hhg_shell {
+  hhg::MacroMesh mesh;
+  int Lf = 0;                          // finest log2(N)
+  std::vector<hhg::Level> levels;      // levels[n]: N = 4 << n
+  hhg::CellGeom* d_geom = nullptr;
+  hhg::Allocator alloc;
+  int q = 0, j = 0;                    // surrogate degree and sampling choice, q = 0: not fitted
+  double* d_red = nullptr;             // reduction scratch (partials + results)
+  int64_t red_len = 0;
+  double* d_cg = nullptr;              // coarse-solver vectors
+  double* d_stage[3] = {nullptr, nullptr, nullptr};  // staging for host-pointer arguments
+  int64_t stage_len = 0;
+
+  hhg::Level& level_of(int L) { return levels.at(L - 2); }
+};
