@@ -1,0 +1,407 @@
+#!/usr/bin/env python
+"""Benchmark of the two-scale (LSQP) multigrid solve on one GB300.
+
+Workload (default): the 3840-macro shell r in [0.55, 1] (icosahedron refined
+twice on the surface, 4 radial layers, 3 tetrahedra per prism) refined to
+N = 64 intervals per macro edge (168,428,034 nodes, 167,117,310 unknowns),
+FP64, LSQP surrogate q = 2 on S_l = M_2, right-hand side uniform[-1, 1]
+(seed 0).  One step is the whole path: the surrogate fit (sampling + least
+squares) followed by V(3,3) cycles from u = 0 until the relative residual is
+<= 1e-8.
+
+value: stencil-row updates per second over the step (GLUP/s): every smoother
+update, residual row and convergence-check row on levels N >= 8, divided by
+the step's device time; the N = 4 coarse solve is not counted.
+
+Reported beside it: the smoother alone (one full sweep of the finest level,
+LSQP and IFEM), the dominant kernel's roofline (finest-level cell-interior
+LSQP smoother, FP64 pipe bound), the end-to-end number through host buffers,
+and the CPU oracle timed on a sample of the same workload.
+
+--impl reference times the CPU oracle (the only reference this method has)
+on the host cores, on the same workload, each step a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLUP/s surrogate smoother vs IFEM; V-cycle s to 1e-8 residual; p50/p99 latency"
+WORKLOADS = {
+    # name: (tang, layers, L, description)
+    "shell3840_N64": (2, 4, 6, "3840 macro cells (icosahedral shell, 2 surface refinements, 4 layers), "
+                               "N=64 intervals per macro edge, r in [0.55, 1]"),
+    "shell480_N64": (1, 2, 6, "480 macro cells (icosahedral shell, 1 surface refinement, 2 layers), N=64, "
+                              "r in [0.55, 1]"),
+    "shell60_N16": (0, 1, 4, "60 macro cells (icosahedral shell, 1 layer), N=16, r in [0.55, 1]"),
+}
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (recipe's nominal figure: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)
+LSQP_FLOPS = {1: 44, 2: 59, 3: 74}   # Table 4.2: 29 + 15 q flops per stencil-based update
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="shell3840_N64")
+    p.add_argument("--q", type=int, default=2)
+    p.add_argument("--j", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--mode", choices=["solve", "smoother"], default="solve",
+                   help="solve: the whole path per step (default); smoother: finest-level sweeps only "
+                        "(for profiling the smoother kernels)")
+    p.add_argument("--op", choices=["lsqp", "ifem"], default="lsqp", help="operator for --mode smoother")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing (replicas only: every rank solves its own shell)
+# ----------------------------------------------------------------------------
+
+def dist_init(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9 or (self.uuid and parts[0] != self.uuid):
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def traffic_record(kernel: str, workload: str):
+    """ncu DRAM bytes per launch of `kernel` on `workload`, if recorded for the
+    current kernel source (profiles/traffic.json, written from an ncu capture);
+    None when absent or when the source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(f"{kernel}@{workload}")
+    if not rec:
+        return None
+    src = open(os.path.join(ROOT, "paper_1608_06473_gb300", "csrc", rec["source"]), "rb").read()
+    if hashlib.sha256(src).hexdigest()[:16] != rec["sha256_16"]:
+        return None
+    return rec["dram_bytes_per_launch"]
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    import paper_1608_06473_gb300 as hhg
+    import synthetic
+
+    torch.cuda.set_device(local)
+    tang, layers, L, desc = WORKLOADS[args.workload]
+    stream = torch.cuda.current_stream()
+    s = hhg.Shell(0.55, 1.0, tang, layers, L, stream=stream)
+    n_total, n_free = s.num_nodes()
+    free_per_level = {l: s.num_nodes(l)[1] for l in range(2, L + 1)}
+    f = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_F)).cuda()
+    u = torch.zeros(n_total, dtype=torch.float64, device="cuda")
+    op = hhg.HHG_OP_LSQP
+    nu1 = nu2 = 3
+
+    def step(fv, uv):
+        s.fit(args.q, args.j, stream=stream)
+        if isinstance(uv, torch.Tensor) and uv.is_cuda:
+            uv.zero_()
+        rel, cycles, _ = s.vcycle(fv, uv, nu1, nu2, max_cycles=60, rtol=1e-8, op=op, stream=stream)
+        return rel[0], cycles
+
+    def updates(cycles):
+        per_cycle = sum((nu1 + nu2 + 1) * free_per_level[l] for l in range(3, L + 1)) + free_per_level[L]
+        return cycles * per_cycle + free_per_level[L]
+
+    for _ in range(args.warmup):
+        step(f, u)
+    torch.cuda.synchronize()
+
+    props = torch.cuda.get_device_properties(local)
+    uuid = "GPU-" + str(props.uuid) if hasattr(props, "uuid") else None
+    clocks = ClockSampler(uuid)
+    hhg.hhg_timing(s.handle, True)
+    launches0 = hhg.hhg_launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    tot_updates, cyc_list, rels = 0, [], []
+    for _ in range(args.steps):
+        rel, cycles = step(f, u)
+        tot_updates += updates(cycles)
+        cyc_list.append(cycles)
+        rels.append(rel)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    launches = hhg.hhg_launch_count() - launches0
+    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ms, world)
+    sm_ms, sm_n = hhg.hhg_timing_read(s.handle, hhg.HHG_T_CELL_SMOOTH)
+    hhg.hhg_timing(s.handle, False)
+
+    # smoother alone: one sweep of the finest level (all 10 steps)
+    def sweep_glups(opcode, reps):
+        uu = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_U)).cuda()
+        s.smooth(f, uu, 1, op=opcode, stream=stream)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.smooth(f, uu, reps, op=opcode, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return n_free * reps / (a.elapsed_time(b) * 1e-3) / 1e9
+
+    g_lsqp = sweep_glups(hhg.HHG_OP_LSQP, 3)
+    g_ifem = sweep_glups(hhg.HHG_OP_IFEM, 1)
+
+    # end to end through host buffers (pinned): H2D of f and u, D2H of u per step
+    e2e = None
+    if not args.no_e2e:
+        fh = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_F)).pin_memory()
+        uh = torch.zeros(n_total, dtype=torch.float64).pin_memory()
+        ke = max(1, min(args.steps, 2))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e_upd = 0
+        for _ in range(ke):
+            uh.zero_()
+            rel, cycles = step(fh, uh)
+            e_upd += updates(cycles)
+        torch.cuda.synchronize()
+        te = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": e_upd * world / te / 1e9, "unit": "GLUP/s", "h2d_bytes_per_step": 16 * n_total,
+               "d2h_bytes_per_step": 8 * n_total, "steps": ke}
+
+    # one smoother launch updates every cell-interior node of the finest level once
+    N = 2 ** L
+    n_cells = 20 * 4 ** tang * layers * 3
+    units_per_launch = n_cells * (N - 1) * (N - 2) * (N - 3) // 6
+    avg_launch_s = sm_ms * 1e-3 / max(sm_n, 1)
+    flops = LSQP_FLOPS[args.q] * units_per_launch
+    achieved = flops / avg_launch_s / 1e12
+    traffic = traffic_record("lsqp_cell_smooth_f64", args.workload)
+    roofline = {"kernel": "lsqp_cell_kernel<double,%d,SMOOTH> (finest level)" % args.q, "bound": "alu",
+                "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": traffic,
+                "launches": sm_n, "avg_launch_ms": avg_launch_s * 1e3,
+                "algorithmic_flops_per_launch": flops,
+                "algorithmic_bytes_per_launch": 24 * units_per_launch,
+                "achieved_hbm_gbs_algorithmic": 24 * units_per_launch / avg_launch_s / 1e9,
+                "peak_note": "FP64 nominal (recipe); HBM measured copy 6794.8 GB/s"}
+    value = tot_updates * world / (ms * 1e-3) / 1e9
+    out = {"metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "shell": desc, "op": "lsqp", "q": args.q, "j": args.j,
+                      "cycle": "V(3,3)", "rtol": 1e-8, "unknowns": n_free, "nodes": n_total,
+                      "l2": "inputs larger than L2 (each FP64 vector %.2f GB)" % (8 * n_total / 1e9),
+                      "parallelism": "replicas" if world > 1 else "single"},
+           "clocks": clk, "gpu_launches": launches, "roofline": roofline,
+           "e2e": e2e,
+           "smoother_glups": {"lsqp": g_lsqp, "ifem": g_ifem, "lsqp_over_ifem": g_lsqp / g_ifem},
+           "vcycle_s_to_1e-8": ms * 1e-3 / args.steps, "cycles": cyc_list, "final_relres": max(rels)}
+    s.close()
+    return out
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (cpu_baseline and the reference arm)
+# ----------------------------------------------------------------------------
+
+def oracle_sample(workload, n_cells, sweeps, seed=7):
+    """Oracle LSQP multicolour Gauss-Seidel sweeps over the interior rows of a
+    seeded sample of macro cells of the workload's shell; returns (updates,
+    seconds) of the sweeps alone (assembly and fit excluded)."""
+    import synthetic
+    from oracle import local as LO
+    from oracle import mesh as M
+    tang, layers, L, _ = WORKLOADS[workload]
+    sh = M.make_shell(tang=tang, layers=layers)
+    N = 2 ** L
+    col = LO.colour_of(N)
+    upd, sec = 0, 0.0
+    for c in synthetic.sample(sh.nC, n_cells, seed):
+        rows, cols, W = LO.interior_rows(sh, N, int(c), "lsqp")
+        idx = np.unique(np.concatenate([rows, cols.ravel()]))
+        lr, lc = np.searchsorted(idx, rows), np.searchsorted(idx, cols)
+        u = synthetic.uniform(len(idx), synthetic.SEED_U)
+        f = synthetic.uniform(len(idx), synthetic.SEED_F)
+        t0 = time.perf_counter()
+        for _ in range(sweeps):
+            LO.interior_colour_steps(lr, lc, W, col, u, f)
+        sec += time.perf_counter() - t0
+        upd += sweeps * len(rows)
+    return upd, sec
+
+
+def cpu_baseline(workload, n_cells=6, sweeps=60):
+    upd, sec = oracle_sample(workload, n_cells, sweeps)
+    return {"value": upd / sec / 1e9, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle LSQP multicolour GS, {sweeps} sweeps over the interior rows of {n_cells} seeded "
+                      f"macro cells of {workload} (FP64 NumPy, one core; assembly and fit excluded)",
+            "seconds": sec}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    n_cells, sweeps = 2, 20
+    for _ in range(args.warmup):
+        oracle_sample(args.workload, 1, 2)
+    upd, sec = 0, 0.0
+    for k in range(args.steps):
+        a, b = oracle_sample(args.workload, n_cells, sweeps, seed=11 + k)
+        upd += a
+        sec += b
+    v = upd / sec / 1e9
+    tang, layers, L, desc = WORKLOADS[args.workload]
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "GLUP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "shell": desc, "op": "lsqp", "q": 2, "j": 2},
+            "cpu_baseline": {"value": v, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
+                             "sample": f"per step: {sweeps} oracle LSQP GS sweeps over {n_cells} seeded macro cells"},
+            "e2e": {"value": v, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_smoother(args):
+    """Finest-level smoother only: setup, fit, `warmup` sweeps, then `steps`
+    sweeps timed with CUDA events on the launching stream."""
+    import torch
+
+    import paper_1608_06473_gb300 as hhg
+    import synthetic
+    tang, layers, L, desc = WORKLOADS[args.workload]
+    stream = torch.cuda.current_stream()
+    s = hhg.Shell(0.55, 1.0, tang, layers, L, stream=stream)
+    n_total, n_free = s.num_nodes()
+    opcode = hhg.HHG_OP_LSQP if args.op == "lsqp" else hhg.HHG_OP_IFEM
+    if opcode == hhg.HHG_OP_LSQP:
+        s.fit(args.q, args.j, stream=stream)
+    f = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_F)).cuda()
+    u = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_U)).cuda()
+    s.smooth(f, u, args.warmup, op=opcode, stream=stream)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    s.smooth(f, u, args.steps, op=opcode, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    s.close()
+    return {"mode": "smoother", "op": args.op, "workload": args.workload, "sweeps": args.steps,
+            "ms_per_sweep": ms / args.steps, "GLUP/s": n_free * args.steps / (ms * 1e-3) / 1e9}
+
+
+def main():
+    args = parse()
+    if args.mode == "smoother":
+        print(json.dumps(run_smoother(args)))
+        return
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    rank, world, local = dist_init(args.gpus)
+    out = run_ours(args, rank, world, local)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args.workload)
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -157,6 +157,26 @@ hhg_status hhg_vcycle(hhg_shell* shell, hhg_op op, hhg_dtype dtype,
                       double rtol, int nrhs, double* relres_out, int* cycles_out,
                       void* stream);
 
+/* ---- Diagnostics (not part of the method) ------------------------------ */
+
+/* Number of CUDA kernels this library has launched in this process. */
+int64_t hhg_launch_count(void);
+
+/* Kernel classes timed by hhg_timing. */
+typedef enum {
+  HHG_T_CELL_SMOOTH = 0,     /* finest-level cell-interior smoother (4 colours) */
+  HHG_T_CELL_RESIDUAL = 1,   /* finest-level cell-interior residual */
+  HHG_T_CELL_APPLY = 2,      /* finest-level cell-interior apply */
+  HHG_T_COUNT = 3
+} hhg_timer;
+
+/* enable != 0: from now on every launch of a timed kernel class is bracketed
+ * by CUDA events on the stream it is launched on; enable = 0 stops and
+ * clears the record.  hhg_timing_read waits for the recorded events and
+ * returns the summed device time (ms) and the number of launches. */
+hhg_status hhg_timing(hhg_shell* shell, int enable);
+hhg_status hhg_timing_read(hhg_shell* shell, int which, double* total_ms, int64_t* launches);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* hhg_last_error(void);
 

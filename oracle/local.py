@@ -76,3 +76,23 @@ def interior_rows(sh: M.Shell, N: int, c: int, op: str = "lsqp", q: int = 2, j: 
     else:
         W = exact_stencils(sh, N, c, ip)
     return rows, cols, W
+
+
+def colour_of(N: int) -> np.ndarray:
+    """Cell-interior colour (i + 2j + 3k) mod 4 of every interior point."""
+    ip = M.interior_points(N)
+    return (ip[:, 0] + 2 * ip[:, 1] + 3 * ip[:, 2]) % 4
+
+
+def interior_colour_steps(rows, cols, W, colour, u, f):
+    """Steps 7-10 of a sweep (cell-interior colours 0..3) restricted to one
+    macro cell: Eq. 5.1 on every node of the colour from the values at the
+    start of the step.  rows/cols index u and f (any numbering); u is
+    updated in place and returned."""
+    for cc in range(4):
+        S = colour == cc
+        acc = f[rows[S]].copy()
+        for w in range(14):
+            acc = acc - W[S, w] * u[cols[S, w]]
+        u[rows[S]] = acc / W[S, 14]
+    return u

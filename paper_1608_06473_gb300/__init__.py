@@ -66,6 +66,8 @@ _SIGS = {
     "hhg_residual": [_P, _I, _I, _I, _P, _P, _P, _I, _P, _P],
     "hhg_smooth": [_P, _I, _I, _I, _P, _P, _I, _I, _P],
     "hhg_vcycle": [_P, _I, _I, _P, _P, _I, _I, _I, ctypes.c_double, _I, _P, _P, _P],
+    "hhg_timing": [_P, _I],
+    "hhg_timing_read": [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
 }
 
 
@@ -83,12 +85,32 @@ def lib() -> ctypes.CDLL:
             fn.restype = ctypes.c_int
         L.hhg_last_error.argtypes = []
         L.hhg_last_error.restype = ctypes.c_char_p
+        L.hhg_launch_count.argtypes = []
+        L.hhg_launch_count.restype = ctypes.c_int64
         _lib = L
     return _lib
 
 
 def exported_symbols():
-    return list(_SIGS) + ["hhg_last_error"]
+    return list(_SIGS) + ["hhg_last_error", "hhg_launch_count"]
+
+
+HHG_T_CELL_SMOOTH, HHG_T_CELL_RESIDUAL, HHG_T_CELL_APPLY = 0, 1, 2
+
+
+def hhg_launch_count() -> int:
+    return lib().hhg_launch_count()
+
+
+def hhg_timing(shell: int, enable: bool):
+    _check(lib().hhg_timing(shell, int(bool(enable))))
+
+
+def hhg_timing_read(shell: int, which: int):
+    """(total device ms, launches) of one timed kernel class."""
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(lib().hhg_timing_read(shell, which, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
 
 
 def hhg_last_error() -> str:

@@ -2,6 +2,7 @@
 // application, smoothing, residual and the V-cycle driver.  See
 // include/hhg.h for the contract of every entry point.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -24,8 +25,10 @@ namespace hhg {
 // ---------------------------------------------------------------------------
 
 static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches{0};
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void* Allocator::alloc(size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -310,6 +313,38 @@ LevelView<double> view<double>(hhg_shell* s, int n) {
 }
 
 // ---------------------------------------------------------------------------
+// diagnostics: CUDA events around the finest-level cell kernels
+// ---------------------------------------------------------------------------
+
+struct TimedScope {
+  hhg_shell* s;
+  int which;
+  cudaStream_t st;
+  cudaEvent_t b = nullptr, e = nullptr;
+  TimedScope(hhg_shell* s_, int n, int which_, cudaStream_t st_) : s(s_), which(which_), st(st_) {
+    if (!s->timing || n != (int)s->levels.size() - 1) return;
+    HHG_CUDA(cudaEventCreate(&b));
+    HHG_CUDA(cudaEventCreate(&e));
+    HHG_CUDA(cudaEventRecord(b, st));
+  }
+  ~TimedScope() {
+    if (!b) return;
+    cudaEventRecord(e, st);
+    s->tevents[which].push_back({b, e});
+  }
+};
+
+static void timing_clear(hhg_shell* s) {
+  for (auto& v : s->tevents) {
+    for (auto& p : v) {
+      cudaEventDestroy(p.first);
+      cudaEventDestroy(p.second);
+    }
+    v.clear();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // operators on one level (device vectors, FP64)
 // ---------------------------------------------------------------------------
 
@@ -324,7 +359,10 @@ static int eff_op(hhg_shell* s, int n, int op) { return (s->levels[n].N >= 8) ? 
 static void op_apply(hhg_shell* s, int n, int op, const double* u, double* y, cudaStream_t st) {
   LevelView<double> v = view<double>(s, n);
   launch_halo(v, u, st);
-  launch_cell(v, eff_op(s, n, op), APPLY, const_cast<double*>(u), y, (const double*)nullptr, nullptr, st);
+  {
+    TimedScope ts(s, n, HHG_T_CELL_APPLY, st);
+    launch_cell(v, eff_op(s, n, op), APPLY, const_cast<double*>(u), y, (const double*)nullptr, nullptr, st);
+  }
   launch_low(v, APPLY, u, y, (const double*)nullptr, nullptr, low_blocks(v.off_C), st);
 }
 
@@ -335,7 +373,10 @@ static void op_residual(hhg_shell* s, int n, int op, const double* u, const doub
   const int nb = low_blocks(v.off_C);
   double* part = s->d_red + 64;
   launch_halo(v, u, st);
-  launch_cell(v, eff_op(s, n, op), RESIDUAL, const_cast<double*>(u), r, f, part, st);
+  {
+    TimedScope ts(s, n, HHG_T_CELL_RESIDUAL, st);
+    launch_cell(v, eff_op(s, n, op), RESIDUAL, const_cast<double*>(u), r, f, part, st);
+  }
   launch_low(v, RESIDUAL, u, r, f, part + v.nC, nb, st);
   launch_sum(part, v.nC + nb, s->d_red + slot, st);
 }
@@ -345,6 +386,7 @@ static void op_smooth(hhg_shell* s, int n, int op, const double* f, double* u, c
   Level& L = s->levels[n];
   for (int t = 0; t < 6; ++t) launch_low_step(v, L.d_step[t], L.step_n[t], u, f, L.d_tmp, st);
   launch_halo(v, (const double*)u, st);
+  TimedScope ts(s, n, HHG_T_CELL_SMOOTH, st);
   launch_cell(v, eff_op(s, n, op), SMOOTH, u, u, f, nullptr, st);
 }
 
@@ -574,6 +616,32 @@ extern "C" {
 
 const char* hhg_last_error(void) { return g_last_error.c_str(); }
 
+int64_t hhg_launch_count(void) { return g_launches.load(); }
+
+hhg_status hhg_timing(hhg_shell* s, int enable) {
+  return guarded([&] {
+    HHG_CHECK(s != nullptr, HHG_EINVAL, "NULL shell");
+    if (!enable) timing_clear(s);
+    s->timing = enable != 0;
+  });
+}
+
+hhg_status hhg_timing_read(hhg_shell* s, int which, double* total_ms, int64_t* launches) {
+  return guarded([&] {
+    HHG_CHECK(s != nullptr, HHG_EINVAL, "NULL shell");
+    HHG_CHECK(which >= 0 && which < HHG_T_COUNT, HHG_EINVAL, "unknown timer");
+    double tot = 0;
+    for (auto& p : s->tevents[which]) {
+      HHG_CUDA(cudaEventSynchronize(p.second));
+      float ms = 0;
+      HHG_CUDA(cudaEventElapsedTime(&ms, p.first, p.second));
+      tot += ms;
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = (int64_t)s->tevents[which].size();
+  });
+}
+
 hhg_status hhg_setup_shell(const hhg_shell_desc* d, void* stream, hhg_shell** out) {
   return guarded([&] {
     HHG_CHECK(d && out, HHG_EINVAL, "NULL argument");
@@ -624,6 +692,7 @@ hhg_status hhg_destroy(hhg_shell* s) {
   return guarded([&] {
     if (!s) return;
     cudaDeviceSynchronize();
+    timing_clear(s);
     s->alloc.release_all();
     delete s;
   });

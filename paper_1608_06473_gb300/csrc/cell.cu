@@ -191,6 +191,7 @@ void launch_lsqp(const LevelView<T>& lv, T* u, T* out, const T* f, double* parti
   if (smem > 48 * 1024) HHG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<lv.nC, CELL_THREADS, smem, st>>>(lv, u, out, f, partial);
   HHG_CUDA(cudaGetLastError());
+  count_launch();
 }
 
 template <class T, Mode MODE>
@@ -267,6 +268,7 @@ void launch_cell(const LevelView<T>& lv, int op, Mode mode, T* u, T* out, const 
     case SMOOTH: ifem_cell_kernel<T, SMOOTH><<<lv.nC, CELL_THREADS, 0, st>>>(lv, u, out, f, partial); break;
   }
   HHG_CUDA(cudaGetLastError());
+  count_launch();
 }
 
 template void launch_cell<double>(const LevelView<double>&, int, Mode, double*, double*, const double*, double*,
@@ -279,6 +281,7 @@ void launch_sample(const LevelView<double>& lv, const uint32_t* pts, int n_pts, 
   if (n == 0) return;
   sample_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(lv, pts, n_pts, b);
   HHG_CUDA(cudaGetLastError());
+  count_launch();
 }
 
 void launch_fit_coef(int nC, int mq, int n_pts, const double* aplus, const double* scale, const double* b,
@@ -286,6 +289,7 @@ void launch_fit_coef(int nC, int mq, int n_pts, const double* aplus, const doubl
   const int64_t n = (int64_t)nC * mq;
   fit_coef_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(nC, mq, n_pts, aplus, scale, b, coef, coef32);
   HHG_CUDA(cudaGetLastError());
+  count_launch();
 }
 
 }  // namespace hhg

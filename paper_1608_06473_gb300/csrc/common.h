@@ -53,8 +53,6 @@ HD bool is_interior(int i, int j, int k, int N) {
 // ---------------------------------------------------------------------------
 enum Dir { ME = 0, MW, MN, MS, MNW, MSE, TC, TW, TS, TSE, BC, BE, BN, BNW, MC, NDIR };
 
-struct DirOffsets { int di[15], dj[15], dk[15]; };
-
 HD int dir_di(int w) { const int t[15] = {1, -1, 0, 0, -1, 1, 0, -1, 0, 1, 0, 1, 0, -1, 0}; return t[w]; }
 HD int dir_dj(int w) { const int t[15] = {0, 0, 1, -1, 1, -1, 0, 0, -1, -1, 0, 0, 1, 1, 0}; return t[w]; }
 HD int dir_dk(int w) { const int t[15] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, -1, -1, -1, -1, 0}; return t[w]; }
@@ -70,6 +68,9 @@ inline int dir_of(int di, int dj, int dk) {
 // three direction indices of its other vertices (filled by kuhn_star()).
 struct Star { int8_t t[24][3]; };
 void kuhn_star(Star* s);
+
+// Counts kernel launches (diagnostics).
+void count_launch(int n = 1);
 
 // ---------------------------------------------------------------------------
 // Status plumbing

@@ -335,6 +335,7 @@ void launch_halo(const LevelView<T>& lv, const T* u, cudaStream_t st) {
   const int64_t n = (int64_t)lv.nC * lv.n_bnd;
   halo_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(lv, u);
   HHG_CUDA(cudaGetLastError());
+  count_launch();
 }
 
 template <class T>
@@ -343,6 +344,7 @@ void launch_low(const LevelView<T>& lv, Mode mode, const T* u, T* out, const T* 
   if (mode == APPLY) low_kernel<T, APPLY><<<nblk, LOW_THREADS, 0, st>>>(lv, u, out, f, partial);
   else low_kernel<T, RESIDUAL><<<nblk, LOW_THREADS, 0, st>>>(lv, u, out, f, partial);
   HHG_CUDA(cudaGetLastError());
+  count_launch();
 }
 
 template <class T>
@@ -351,6 +353,7 @@ void launch_low_step(const LevelView<T>& lv, const int* list, int n, T* u, const
   low_step_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(lv, list, n, u, f, tmp);
   scatter_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(list, n, tmp, u);
   HHG_CUDA(cudaGetLastError());
+  count_launch(2);
 }
 
 template <class T>
@@ -358,6 +361,7 @@ void launch_zero_list(const int* list, int n, T* v, cudaStream_t st) {
   if (n == 0) return;
   zero_list_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(list, n, v);
   HHG_CUDA(cudaGetLastError());
+  count_launch();
 }
 
 template <class T>
@@ -367,6 +371,7 @@ void launch_prolong_add(const LevelView<T>& fine, const LevelView<T>& coarse, co
   if (n) prolong_cell_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(fine, coarse, ec, uf);
   prolong_low_kernel<T><<<grid_for(fine.off_C, 256), 256, 0, st>>>(fine, low_par, ec, uf);
   HHG_CUDA(cudaGetLastError());
+  count_launch(n ? 2 : 1);
 }
 
 template <class T>
@@ -376,33 +381,39 @@ void launch_restrict(const LevelView<T>& fine, const LevelView<T>& coarse, const
   if (n) restrict_cell_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(fine, coarse, rf, rc);
   restrict_low_kernel<T><<<grid_for(coarse.off_C, 256), 256, 0, st>>>(fine, coarse, clf, rf, rc);
   HHG_CUDA(cudaGetLastError());
+  count_launch(n ? 2 : 1);
 }
 
 void launch_sum(const double* partial, int n, double* out, cudaStream_t st) {
   sum_kernel<<<1, 1024, 0, st>>>(partial, n, out);
   HHG_CUDA(cudaGetLastError());
+  count_launch();
 }
 
 void launch_dot_partial(const double* a, const double* b, int64_t n, double* partial, int nblk, cudaStream_t st) {
   dot_kernel<<<nblk, 256, 0, st>>>(a, b, n, partial);
   HHG_CUDA(cudaGetLastError());
+  count_launch();
 }
 
 void launch_cg_update(double* x, double* r, double* z, const double* p, const double* q, const double* dinv,
                       const double* num, const double* den, int64_t n, cudaStream_t st) {
   cg_update_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, r, z, p, q, dinv, num, den, n);
   HHG_CUDA(cudaGetLastError());
+  count_launch();
 }
 
 void launch_cg_dir(double* p, const double* z, const double* num_new, const double* num_old, int64_t n,
                    cudaStream_t st) {
   cg_dir_kernel<<<grid_for(n, 256), 256, 0, st>>>(p, z, num_new, num_old, n);
   HHG_CUDA(cudaGetLastError());
+  count_launch();
 }
 
 void launch_coarse_diag(const LevelView<double>& lv, double* dinv, cudaStream_t st) {
   coarse_diag_kernel<<<grid_for(lv.n_total, 128), 128, 0, st>>>(lv, dinv);
   HHG_CUDA(cudaGetLastError());
+  count_launch();
 }
 
 template <class T>
@@ -410,6 +421,7 @@ void launch_copy_cast(const double* src, T* dst, int64_t n, cudaStream_t st) {
   if (n == 0) return;
   copy_cast_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(src, dst, n);
   HHG_CUDA(cudaGetLastError());
+  count_launch();
 }
 
 void launch_low_assemble(const LevelView<double>& lv, int pass, const int64_t* inc_ptr, const int* inc_cb,
@@ -418,6 +430,7 @@ void launch_low_assemble(const LevelView<double>& lv, int pass, const int64_t* i
   low_assemble_kernel<<<grid_for(lv.off_C, 64), 64, 0, st>>>(lv, pass, inc_ptr, inc_cb, row_len, sell_ptr, sell_col,
                                                              sell_val, diag);
   HHG_CUDA(cudaGetLastError());
+  count_launch();
 }
 
 #define INST(T)                                                                                                   \

@@ -121,5 +121,9 @@ struct hhg_shell {
   double* d_stage[3] = {nullptr, nullptr, nullptr};  // staging for host-pointer arguments
   int64_t stage_len = 0;
 
+  // diagnostics: CUDA-event pairs around timed kernel launches
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tevents[HHG_T_COUNT];
+
   hhg::Level& level_of(int L) { return levels.at(L - 2); }
 };
