@@ -96,3 +96,39 @@ def interior_colour_steps(rows, cols, W, colour, u, f):
             acc = acc - W[S, w] * u[cols[S, w]]
         u[rows[S]] = acc / W[S, 14]
     return u
+
+
+def node_rows(sh: M.Shell, N: int, nodes, op: str = "ifem", q: int = 2, j: int = 2):
+    """Rows of L_l (or L~_l for op='lsqp' at cell-interior nodes) for a list of
+    canonical nodes of any primitive, assembled from the cells that contain
+    them: {node: {column: weight}}.  Lower-primitive rows are exact in both
+    operators (Sec. 3.4)."""
+    cache = {}
+
+    def cell(c):
+        if c not in cache:
+            cache[c] = (cell_map(sh, N, c), cell_matrix(sh, N, c))
+        return cache[c]
+
+    out = {}
+    for n in nodes:
+        verts = set(M.primitive_of(sh, N, n))
+        row = {}
+        for c in np.flatnonzero([verts <= set(int(x) for x in cv) for cv in sh.cells]):
+            cm, A = cell(int(c))
+            loc = np.flatnonzero(cm == n)
+            if len(loc) == 0:
+                continue
+            r = A.getrow(int(loc[0]))
+            for jj, a in zip(r.indices, r.data):
+                row[int(cm[jj])] = row.get(int(cm[jj]), 0.0) + a
+        out[n] = row
+    off_C = M.offsets(sh, N)[2]
+    if op == "lsqp" and N >= 8:
+        for n in nodes:
+            if n >= off_C:
+                c = (n - off_C) // M.n_cell_nodes(N)
+                rows, cols, W = interior_rows(sh, N, int(c), "lsqp", q, j)
+                k = int(np.flatnonzero(rows == n)[0])
+                out[n] = {int(cols[k, w]): float(W[k, w]) for w in range(15)}
+    return out

@@ -153,7 +153,7 @@ def n_face_nodes(N: int) -> int:
 
 
 def n_cell_nodes(N: int) -> int:
-    """n_l of Eq. 2.2 with N = 2^(l+2)."""
+    """n_l of Eq. 2.5 with N = 2^(l+2)."""
     return (N - 1) * (N - 2) * (N - 3) // 6
 
 
@@ -339,3 +339,42 @@ def support_kind(level: Level, idx: np.ndarray) -> np.ndarray:
     """0 vertex, 1 edge, 2 face, 3 cell interior for canonical indices."""
     idx = np.asarray(idx)
     return np.select([idx < level.off_E, idx < level.off_F, idx < level.off_C], [0, 1, 2], 3)
+
+
+def offsets(sh: Shell, N: int):
+    """(off_E, off_F, off_C, n_total) of the canonical order at level N."""
+    return _prim_offsets(sh, N)
+
+
+def dirichlet_of(sh: Shell, N: int, idx: np.ndarray) -> np.ndarray:
+    """Dirichlet flag of canonical indices without building the level: a node
+    is Dirichlet when its primitive's vertices all lie on r1 or all on r2."""
+    off_E, off_F, off_C, _ = _prim_offsets(sh, N)
+    idx = np.asarray(idx, dtype=np.int64)
+    lay, M = sh.vert_layer, sh.layers
+    out = np.zeros(len(idx), dtype=bool)
+    v = idx < off_E
+    out[v] = np.isin(lay[idx[v]], (0, M))
+    e = (idx >= off_E) & (idx < off_F)
+    if e.any():
+        E = sh.edges[(idx[e] - off_E) // (N - 1)]
+        la = lay[E]
+        out[e] = (la[:, 0] == la[:, 1]) & np.isin(la[:, 0], (0, M))
+    f = (idx >= off_F) & (idx < off_C)
+    if f.any():
+        F = sh.faces[(idx[f] - off_F) // n_face_nodes(N)]
+        la = lay[F]
+        out[f] = (la[:, 0] == la[:, 1]) & (la[:, 1] == la[:, 2]) & np.isin(la[:, 0], (0, M))
+    return out
+
+
+def primitive_of(sh: Shell, N: int, idx: int):
+    """Vertex ids of the primitive that owns canonical node idx (1 to 4)."""
+    off_E, off_F, off_C, _ = _prim_offsets(sh, N)
+    if idx < off_E:
+        return (int(idx),)
+    if idx < off_F:
+        return tuple(int(x) for x in sh.edges[(idx - off_E) // (N - 1)])
+    if idx < off_C:
+        return tuple(int(x) for x in sh.faces[(idx - off_F) // n_face_nodes(N)])
+    return tuple(int(x) for x in sh.cells[(idx - off_C) // n_cell_nodes(N)])

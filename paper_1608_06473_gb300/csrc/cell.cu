@@ -143,6 +143,121 @@ __global__ void __launch_bounds__(CELL_THREADS) lsqp_cell_kernel(LevelView<T> lv
   }
 }
 
+// FP64 surrogate kernel with the weights evaluated in exact 64-bit integer
+// arithmetic.  GB300 issues FP64 at a small fraction of its FP32/INT32 rate,
+// and evaluating the 15 line polynomials is half of the FP64 work of an
+// update.  Here the line coefficients are scaled by 2^E (E per cell, chosen
+// so that every partial sum stays below 2^62) and rounded to integers once
+// per line; per node the polynomial is evaluated by integer Horner (exact) and
+// converted to FP64 once per weight.  The weights equal the FP64 ones to the
+// rounding of the conversion; the factor 2^-E is applied once per node.
+__device__ __forceinline__ long long horner_i64(const long long* C, int i, int Q) {
+  long long v = C[Q];
+  for (int a = Q - 1; a >= 0; --a) v = v * (long long)i + C[a];
+  return v;
+}
+
+template <int Q, Mode MODE, int THREADS>
+__global__ void __launch_bounds__(THREADS) lsqp_cell_kernel_iw(LevelView<double> lv, double* u, double* out,
+                                                                const double* f, double* partial) {
+  constexpr int MQ = (Q + 1) * (Q + 2) * (Q + 3) / 6;
+  constexpr int NSLOT = (MODE == SMOOTH) ? 4 : 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sA = reinterpret_cast<double*>(smem_raw);          // [15][MQ]
+  long long* ring = reinterpret_cast<long long*>(sA + 15 * MQ);  // [NSLOT][NL][15][Q+1]
+  __shared__ double s_bound[THREADS / 32];
+  const int c = blockIdx.x;
+  const int N = lv.N;
+  const int NL = N - 3;
+  for (int t = threadIdx.x; t < 15 * MQ; t += blockDim.x) sA[t] = lv.coef[(int64_t)c * 15 * MQ + t];
+  __syncthreads();
+  // B = max_w sum_t |A_wt| N^deg(t) bounds |c_a(j,k)| i^a for every line and node
+  double bnd = 0.0;
+  if (threadIdx.x < 15) {
+    int t = 0;
+    for (int a = 0; a <= Q; ++a)
+      for (int d = 0; d <= Q - a; ++d)
+        for (int b = 0; b <= Q - a - d; ++b, ++t)
+          bnd += fabs(sA[threadIdx.x * MQ + t]) * ldexp(1.0, (a + b + d) * (31 - __clz(N)));  // N = 2^L
+  }
+  for (int o = 16; o > 0; o >>= 1) bnd = fmax(bnd, __shfl_down_sync(0xffffffffu, bnd, o));
+  if ((threadIdx.x & 31) == 0) s_bound[threadIdx.x >> 5] = bnd;
+  __syncthreads();
+  double B = 0.0;
+  for (int w = 0; w < THREADS / 32; ++w) B = fmax(B, s_bound[w]);
+  const int ex = ilogb(B > 0.0 ? B : 1.0) + 1;  // B < 2^ex
+  const int E = 60 - ex;          // B 2^E < 2^60: |C2 i^2 + C1 i + C0| < 3 * 2^60
+  const double scale = ldexp(1.0, E), inv_scale = ldexp(1.0, -E);
+  double nrm = 0.0;
+
+  auto prologue = [&](int k) {
+    const int slot = (NSLOT == 4) ? (k & 3) : 0;
+    for (int jj = threadIdx.x; jj < N - 2 - k; jj += blockDim.x) {
+      long long* dst = ring + ((slot * NL + jj) * 15) * (Q + 1);
+#pragma unroll 1
+      for (int w = 0; w < 15; ++w) {
+        double cl[Q + 1];
+        line_coeffs<double, Q>(sA + w * MQ, (double)(jj + 1), (double)k, cl);
+#pragma unroll
+        for (int a = 0; a <= Q; ++a) dst[w * (Q + 1) + a] = __double2ll_rn(cl[a] * scale);
+      }
+    }
+  };
+  auto process = [&](int k, int beg, int end) {
+    const int slot = (NSLOT == 4) ? (k & 3) : 0;
+    for (int t = beg + threadIdx.x; t < end; t += blockDim.x) {
+      const uint32_t p = lv.plane_nodes[t];
+      const int i = unpack_i(p), j = unpack_j(p);
+      const long long* cl = ring + ((slot * NL + (j - 1)) * 15) * (Q + 1);
+      double sw[15];
+#pragma unroll
+      for (int w = 0; w < 15; ++w) sw[w] = (double)horner_i64(cl + w * (Q + 1), i, Q);
+      const int64_t I = lv.off_C + (int64_t)c * lv.n_int + lin_interior(i, j, k, N);
+      if (MODE == SMOOTH) {
+        double acc = f[I] * scale;
+#pragma unroll
+        for (int w = 0; w < 14; ++w) acc = fma(-sw[w], load_pt(lv, (const double*)u, c, i + DI(w), j + DJ(w), k + DK(w)), acc);
+        u[I] = acc / sw[MC];
+      } else {
+        double acc = sw[MC] * u[I];
+#pragma unroll
+        for (int w = 0; w < 14; ++w) acc = fma(sw[w], load_pt(lv, (const double*)u, c, i + DI(w), j + DJ(w), k + DK(w)), acc);
+        if (MODE == APPLY) {
+          out[I] = acc * inv_scale;
+        } else {
+          const double r = fma(-inv_scale, acc, f[I]);
+          out[I] = r;
+          nrm += r * r;
+        }
+      }
+    }
+  };
+
+  if (MODE == SMOOTH) {
+    for (int s = 0; s <= N - 1; ++s) {
+      if (s + 1 <= N - 3) prologue(s + 1);
+      __syncthreads();
+#pragma unroll 1
+      for (int cc = 0; cc < 4; ++cc) {
+        const int k = s + 1 - cc;
+        if (k >= 1 && k <= N - 3) process(k, lv.plane_off[k * 4 + cc], lv.plane_off[k * 4 + cc + 1]);
+        __syncthreads();
+      }
+    }
+  } else {
+    for (int k = 1; k <= N - 3; ++k) {
+      prologue(k);
+      __syncthreads();
+      process(k, lv.plane_off[k * 4], lv.plane_off[k * 4 + 4]);
+      __syncthreads();
+    }
+  }
+  if (MODE == RESIDUAL) {
+    const double tot = block_sum(nrm);
+    if (threadIdx.x == 0) partial[c] = tot;
+  }
+}
+
 template <class T, Mode MODE>
 __global__ void __launch_bounds__(CELL_THREADS) ifem_cell_kernel(LevelView<T> lv, T* u, T* out, const T* f,
                                                                   double* partial) {
@@ -187,6 +302,14 @@ void launch_lsqp(const LevelView<T>& lv, T* u, T* out, const T* f, double* parti
   constexpr int MQ = (Q + 1) * (Q + 2) * (Q + 3) / 6;
   constexpr int NSLOT = (MODE == SMOOTH) ? 4 : 1;
   const size_t smem = sizeof(T) * (15 * MQ + (size_t)NSLOT * (lv.N - 3) * 15 * (Q + 1));
+  if constexpr (sizeof(T) == 8) {
+    auto k2 = lsqp_cell_kernel_iw<Q, MODE, 256>;
+    if (smem > 48 * 1024) HHG_CUDA(cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k2<<<lv.nC, 256, smem, st>>>(lv, u, out, f, partial);
+    HHG_CUDA(cudaGetLastError());
+    count_launch();
+    return;
+  }
   auto kern = lsqp_cell_kernel<T, Q, MODE>;
   if (smem > 48 * 1024) HHG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<lv.nC, CELL_THREADS, smem, st>>>(lv, u, out, f, partial);
