@@ -4,7 +4,7 @@
 // intervals per edge is (i, j, k) with i, j, k >= 0 and i + j + k <= N; its
 // barycentric weights are (N - i - j - k, i, j, k) over the cell's vertices
 // in ascending global id.  Interior points (i, j, k >= 1, i + j + k <= N - 1)
-// form the volume primitive; their count is n_l of Eq. 2.2.
+// form the volume primitive; their count is n_l of Eq. 2.5.
 #pragma once
 
 #include <cstdint>
