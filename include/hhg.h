@@ -157,6 +157,34 @@ hhg_status hhg_vcycle(hhg_shell* shell, hhg_op op, hhg_dtype dtype,
                       double rtol, int nrhs, double* relres_out, int* cycles_out,
                       void* stream);
 
+/* ---- Residual without allocation (no counterpart in the paper) ----------
+ * Some callers cannot allocate device memory at the moment they need a
+ * residual: code in a latency-critical loop that must not stall on the
+ * device-wide synchronisation cudaMalloc/cudaFree can imply, and processes
+ * whose device memory is reserved up front by a pool allocator (a framework's
+ * caching allocator), where a raw cudaMalloc fails or fragments the pool.
+ * For them this entry
+ * point computes the same r = f - L u and ||r||^2 as hhg_residual without
+ * allocating anything: the per-block partial sums of the norm go to a fixed
+ * array of HHG_NOALLOC_SCRATCH doubles (128 KiB) that lives in the library
+ * image; every GPU that loads the library holds it until the process exits.
+ *   - FP64, one right-hand side, device pointers only (host pointers would
+ *     need staging buffers: HHG_EINVAL);
+ *   - norm2_dev: device address of one double that receives ||r||_2^2;
+ *     nothing is copied to the host and the call does not wait;
+ *   - a level needs (macro cells + lower-primitive blocks) partial slots;
+ *     levels that need more than HHG_NOALLOC_SCRATCH are rejected with
+ *     HHG_EINVAL (the 3840-cell shell needs 7936);
+ *   - the first call on a device looks up the array's device address and
+ *     caches it; make that first call before any stream capture;
+ *   - all calls share the array and it keeps the last call's partial sums:
+ *     calls whose work overlaps on the GPU (different streams, or different
+ *     host threads) race on it and must be serialised by the caller.  Each
+ *     call overwrites every slot it reads, so no clearing is needed. */
+#define HHG_NOALLOC_SCRATCH 16384
+hhg_status hhg_residual_noalloc(hhg_shell* shell, int L, hhg_op op, const double* u,
+                                const double* f, double* r, double* norm2_dev, void* stream);
+
 /* ---- Diagnostics (not part of the method) ------------------------------ */
 
 /* Number of CUDA kernels this library has launched in this process. */

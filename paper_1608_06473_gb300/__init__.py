@@ -66,6 +66,7 @@ _SIGS = {
     "hhg_residual": [_P, _I, _I, _I, _P, _P, _P, _I, _P, _P],
     "hhg_smooth": [_P, _I, _I, _I, _P, _P, _I, _I, _P],
     "hhg_vcycle": [_P, _I, _I, _P, _P, _I, _I, _I, ctypes.c_double, _I, _P, _P, _P],
+    "hhg_residual_noalloc": [_P, _I, _I, _P, _P, _P, _P, _P],
     "hhg_timing": [_P, _I],
     "hhg_timing_read": [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
 }
@@ -207,6 +208,15 @@ def hhg_vcycle(shell: int, op: int, dtype: int, f, u, nu1: int = 3, nu2: int = 3
     if st != HHG_OK and (st != HHG_ENOCONV or raise_on_noconv):
         raise HHGError(st, hhg_last_error())
     return rel, cyc.value, st
+
+
+HHG_NOALLOC_SCRATCH = 16384
+
+
+def hhg_residual_noalloc(shell: int, L: int, op: int, u, f, r, norm2_dev, stream=None):
+    """r = f - L u and ||r||^2 into the device double norm2_dev, allocating
+    nothing (device pointers only; see include/hhg.h)."""
+    _check(lib().hhg_residual_noalloc(shell, L, op, _ptr(u), _ptr(f), _ptr(r), _ptr(norm2_dev), _stream(stream)))
 
 
 class Shell:

@@ -3,6 +3,7 @@
 // include/hhg.h for the contract of every entry point.
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -826,3 +827,56 @@ hhg_status hhg_vcycle(hhg_shell* s, hhg_op op, hhg_dtype dtype, const void* f, v
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Residual without allocation: partial sums in a fixed device array
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// The array itself.  In host code its name is only a host-side stand-in;
+// kernels get its device address from cudaGetSymbolAddress.
+static __device__ __align__(256) double g_noalloc_scratch[HHG_NOALLOC_SCRATCH];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the array on the current device, looked up once per
+// device (with that device current).
+double* noalloc_scratch() {
+  int dev = 0;
+  HHG_CUDA(cudaGetDevice(&dev));
+  HHG_CHECK(dev >= 0 && dev < kMaxDevices, HHG_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    HHG_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  return g_noalloc_ptr[dev];
+}
+
+}  // namespace
+
+extern "C" hhg_status hhg_residual_noalloc(hhg_shell* s, int L, hhg_op op, const double* u, const double* f,
+                                           double* r, double* norm2_dev, void* stream) {
+  return guarded([&] {
+    const int n = level_index(s, L);
+    check_op(s, n, op);
+    HHG_CHECK(u && f && r && norm2_dev, HHG_EINVAL, "NULL argument");
+    for (const void* p : {(const void*)u, (const void*)f, (const void*)r, (const void*)norm2_dev})
+      HHG_CHECK(!is_host_ptr(p), HHG_EINVAL, "hhg_residual_noalloc takes device pointers only");
+    LevelView<double> v = view<double>(s, n);
+    const int nb = low_blocks(v.off_C);
+    HHG_CHECK((int64_t)v.nC + nb <= HHG_NOALLOC_SCRATCH, HHG_EINVAL,
+              "level needs " + std::to_string((int64_t)v.nC + nb) + " partial slots, more than HHG_NOALLOC_SCRATCH (" +
+                  std::to_string(HHG_NOALLOC_SCRATCH) + ")");
+    double* part = noalloc_scratch();
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_halo(v, u, st);
+    launch_cell(v, eff_op(s, n, op), RESIDUAL, const_cast<double*>(u), r, f, part, st);
+    launch_low(v, RESIDUAL, u, r, f, part + v.nC, nb, st);
+    launch_sum(part, v.nC + nb, norm2_dev, st);
+  });
+}
