@@ -224,6 +224,10 @@ def run_ours(args, rank, world, local):
     ms = ev0.elapsed_time(ev1)
     ms = max_over_ranks(ms, world)
     sm_ms, sm_n = hhg.hhg_timing_read(s.handle, hhg.HHG_T_CELL_SMOOTH)
+    breakdown = {}
+    for name, tid in hhg.TIMERS.items():
+        ms_t, cnt = hhg.hhg_timing_read(s.handle, tid)
+        breakdown[name] = {"ms_per_step": ms_t / args.steps, "count_per_step": cnt / args.steps}
     hhg.hhg_timing(s.handle, False)
 
     # smoother alone: one sweep of the finest level (all 10 steps)
@@ -267,7 +271,8 @@ def run_ours(args, rank, world, local):
     flops = LSQP_FLOPS[args.q] * units_per_launch
     achieved = flops / avg_launch_s / 1e12
     traffic = traffic_record("lsqp_cell_smooth_f64", args.workload)
-    roofline = {"kernel": "lsqp_cell_kernel<double,%d,SMOOTH> (finest level)" % args.q, "bound": "alu",
+    roofline = {"kernel": "lsqp_node_kernel<%d,SMOOTH> (finest level; one sweep = 4 colour launches)" % args.q,
+                "bound": "alu",
                 "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": traffic,
                 "launches": sm_n, "avg_launch_ms": avg_launch_s * 1e3,
@@ -286,7 +291,8 @@ def run_ours(args, rank, world, local):
            "clocks": clk, "gpu_launches": launches, "roofline": roofline,
            "e2e": e2e,
            "smoother_glups": {"lsqp": g_lsqp, "ifem": g_ifem, "lsqp_over_ifem": g_lsqp / g_ifem},
-           "vcycle_s_to_1e-8": ms * 1e-3 / args.steps, "cycles": cyc_list, "final_relres": max(rels)}
+           "vcycle_s_to_1e-8": ms * 1e-3 / args.steps, "cycles": cyc_list, "final_relres": max(rels),
+           "breakdown": breakdown}
     s.close()
     return out
 

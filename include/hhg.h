@@ -195,13 +195,19 @@ typedef enum {
   HHG_T_CELL_SMOOTH = 0,     /* finest-level cell-interior smoother (4 colours) */
   HHG_T_CELL_RESIDUAL = 1,   /* finest-level cell-interior residual */
   HHG_T_CELL_APPLY = 2,      /* finest-level cell-interior apply */
-  HHG_T_COUNT = 3
+  HHG_T_COARSE = 3,          /* coarsest-level solves; count = CG iterations */
+  HHG_T_FIT = 4,             /* hhg_fit_surrogate calls */
+  HHG_T_SMOOTH = 5,          /* full sweeps on every level (all 10 steps) */
+  HHG_T_RESIDUAL = 6,        /* residuals on every level */
+  HHG_T_TRANSFER = 7,        /* restrictions and prolongations */
+  HHG_T_COUNT = 8
 } hhg_timer;
 
-/* enable != 0: from now on every launch of a timed kernel class is bracketed
- * by CUDA events on the stream it is launched on; enable = 0 stops and
- * clears the record.  hhg_timing_read waits for the recorded events and
- * returns the summed device time (ms) and the number of launches. */
+/* enable != 0: from now on every launch of a timed class is bracketed by
+ * CUDA events on the stream it runs on; enable = 0 stops and clears the
+ * record.  hhg_timing_read waits for the recorded events and returns the
+ * summed stream time (ms) and the number of bracketed calls (for
+ * HHG_T_COARSE: the number of conjugate-gradient iterations). */
 hhg_status hhg_timing(hhg_shell* shell, int enable);
 hhg_status hhg_timing_read(hhg_shell* shell, int which, double* total_ms, int64_t* launches);
 

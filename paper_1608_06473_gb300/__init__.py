@@ -97,6 +97,9 @@ def exported_symbols():
 
 
 HHG_T_CELL_SMOOTH, HHG_T_CELL_RESIDUAL, HHG_T_CELL_APPLY = 0, 1, 2
+HHG_T_COARSE, HHG_T_FIT, HHG_T_SMOOTH, HHG_T_RESIDUAL, HHG_T_TRANSFER = 3, 4, 5, 6, 7
+TIMERS = {"cell_smooth_finest": 0, "cell_residual_finest": 1, "cell_apply_finest": 2, "coarse_solve": 3, "fit": 4,
+          "smooth_all_levels": 5, "residual_all_levels": 6, "transfers": 7}
 
 
 def hhg_launch_count() -> int:

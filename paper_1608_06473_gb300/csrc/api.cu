@@ -145,6 +145,15 @@ static void build_level(hhg_shell* s, int n, cudaStream_t st) {
   for (int k = 1; k < N; ++k)
     for (int j = 1; j < N - k; ++j)
       for (int i = 1; i < N - j - k; ++i) int_ijk.push_back(pack_ijk(i, j, k));
+  std::vector<uint32_t> colour_nodes;
+  for (int cc = 0; cc < 4; ++cc) {
+    L.colour_off[cc] = (int)colour_nodes.size();
+    for (int k = 1; k < N; ++k)
+      for (int j = 1; j < N - k; ++j)
+        for (int i = 1; i < N - j - k; ++i)
+          if ((i + 2 * j + 3 * k) % 4 == cc) colour_nodes.push_back(pack_ijk(i, j, k));
+  }
+  L.colour_off[4] = (int)colour_nodes.size();
   std::vector<uint32_t> bnd_ijk;
   std::vector<int> bnd_slot((size_t)lay.n_full, -1);
   for (int k = 0; k <= N; ++k)
@@ -204,6 +213,7 @@ static void build_level(hhg_shell* s, int n, cudaStream_t st) {
   L.d_plane_nodes = upload(A, plane_nodes, st);
   L.d_plane_off = upload(A, plane_off, st);
   L.d_int_ijk = upload(A, int_ijk, st);
+  L.d_colour_nodes = upload(A, colour_nodes, st);
   L.d_bnd_ijk = upload(A, bnd_ijk, st);
   L.d_bnd_slot = upload(A, bnd_slot, st);
   L.d_halo_src = upload(A, halo_src, st);
@@ -309,6 +319,9 @@ LevelView<double> view<double>(hhg_shell* s, int n) {
   v.geom = s->d_geom; v.plane_nodes = L.d_plane_nodes; v.plane_off = L.d_plane_off; v.int_ijk = L.d_int_ijk;
   v.bnd_ijk = L.d_bnd_ijk; v.bnd_slot = L.d_bnd_slot; v.halo_src = L.d_halo_src; v.ghost = L.d_ghost64;
   v.coef = L.d_coef; v.q = (L.d_coef && L.N >= 8) ? s->q : 0;
+  v.line64 = L.d_line64; v.cell_e = L.d_cell_e; v.n_lines = (int)n_cell_lines(L.N);
+  v.colour_nodes = L.d_colour_nodes;
+  for (int cc = 0; cc < 5; ++cc) v.colour_off[cc] = L.colour_off[cc];
   v.sell_ptr = L.d_sell_ptr; v.sell_col = L.d_sell_col; v.sell_val = L.d_sell_val; v.low_diag = L.d_low_diag;
   return v;
 }
@@ -322,8 +335,9 @@ struct TimedScope {
   int which;
   cudaStream_t st;
   cudaEvent_t b = nullptr, e = nullptr;
+  // n = level index, or -1 for classes timed on every level
   TimedScope(hhg_shell* s_, int n, int which_, cudaStream_t st_) : s(s_), which(which_), st(st_) {
-    if (!s->timing || n != (int)s->levels.size() - 1) return;
+    if (!s->timing || (n >= 0 && n != (int)s->levels.size() - 1)) return;
     HHG_CUDA(cudaEventCreate(&b));
     HHG_CUDA(cudaEventCreate(&e));
     HHG_CUDA(cudaEventRecord(b, st));
@@ -336,6 +350,7 @@ struct TimedScope {
 };
 
 static void timing_clear(hhg_shell* s) {
+  s->cg_iters = 0;
   for (auto& v : s->tevents) {
     for (auto& p : v) {
       cudaEventDestroy(p.first);
@@ -370,6 +385,7 @@ static void op_apply(hhg_shell* s, int n, int op, const double* u, double* y, cu
 // r = f - L u; the squared norm lands in d_red[slot] (device).
 static void op_residual(hhg_shell* s, int n, int op, const double* u, const double* f, double* r, int slot,
                         cudaStream_t st) {
+  TimedScope all(s, -1, HHG_T_RESIDUAL, st);
   LevelView<double> v = view<double>(s, n);
   const int nb = low_blocks(v.off_C);
   double* part = s->d_red + 64;
@@ -383,6 +399,7 @@ static void op_residual(hhg_shell* s, int n, int op, const double* u, const doub
 }
 
 static void op_smooth(hhg_shell* s, int n, int op, const double* f, double* u, cudaStream_t st) {
+  TimedScope all(s, -1, HHG_T_SMOOTH, st);
   LevelView<double> v = view<double>(s, n);
   Level& L = s->levels[n];
   for (int t = 0; t < 6; ++t) launch_low_step(v, L.d_step[t], L.step_n[t], u, f, L.d_tmp, st);
@@ -403,6 +420,7 @@ static double read_scalar(hhg_shell* s, int slot, cudaStream_t st) {
 // Gauss-Seidel as coarse solver, Sec. 4; an exact solve keeps the cycle
 // independent of that choice).
 static void coarse_solve(hhg_shell* s, const double* f, double* x, cudaStream_t st) {
+  TimedScope all(s, -1, HHG_T_COARSE, st);
   Level& L = s->levels[0];
   const int64_t n = L.lay.n_total;
   double* r = s->d_cg;
@@ -436,6 +454,7 @@ static void coarse_solve(hhg_shell* s, const double* f, double* x, cudaStream_t 
   dot(r, z, RZ);
   const double tol2 = 1e-26 * ff;
   for (int it = 0; it < 20000; ++it) {
+    ++s->cg_iters;
     op_apply(s, 0, HHG_OP_IFEM, p, q, st);
     dot(p, q, PQ);
     launch_cg_update(x, r, z, p, q, dinv, s->d_red + RZ, s->d_red + PQ, n, st);
@@ -462,11 +481,17 @@ static void vcycle_rec(hhg_shell* s, int n, int op, const double* f, double* u, 
   for (int t = 0; t < nu1; ++t) op_smooth(s, n, op, f, u, st);
   op_residual(s, n, op, u, f, L.d_r, 8, st);
   LevelView<double> vf = view<double>(s, n), vc = view<double>(s, n - 1);
-  launch_restrict(vf, vc, C.d_coarse_low_fine, (const double*)L.d_r, C.d_f, st);
+  {
+    TimedScope tr(s, -1, HHG_T_TRANSFER, st);
+    launch_restrict(vf, vc, C.d_coarse_low_fine, (const double*)L.d_r, C.d_f, st);
+  }
   HHG_CUDA(cudaMemsetAsync(C.d_u, 0, sizeof(double) * C.lay.n_total, st));
   vcycle_rec(s, n - 1, op, C.d_f, C.d_u, nu1, nu2, st);
-  launch_halo(vc, (const double*)C.d_u, st);
-  launch_prolong_add(vf, vc, L.d_low_par, (const double*)C.d_u, u, st);
+  {
+    TimedScope tr(s, -1, HHG_T_TRANSFER, st);
+    launch_halo(vc, (const double*)C.d_u, st);
+    launch_prolong_add(vf, vc, L.d_low_par, (const double*)C.d_u, u, st);
+  }
   for (int t = 0; t < nu2; ++t) op_smooth(s, n, op, f, u, st);
 }
 
@@ -475,6 +500,7 @@ static void vcycle_rec(hhg_shell* s, int n, int op, const double* f, double* u, 
 // ---------------------------------------------------------------------------
 
 static void fit(hhg_shell* s, int q, int j, cudaStream_t st) {
+  TimedScope all(s, -1, HHG_T_FIT, st);
   const int mq = n_coeffs(q);
   for (size_t n = 0; n < s->levels.size(); ++n) {
     Level& L = s->levels[n];
@@ -509,10 +535,15 @@ static void fit(hhg_shell* s, int q, int j, cudaStream_t st) {
     uint32_t* d_pts = upload(A, pts, st);
     double* d_P = upload(A, P, st);
     double* d_sc = upload(A, sc, st);
-    if (L.d_coef) { A.release(L.d_coef); L.d_coef = nullptr; }
-    if (L.d_coef32) { A.release(L.d_coef32); L.d_coef32 = nullptr; }
-    L.d_coef = A.alloc_n<double>((size_t)L.lay.nC * 15 * mq);
-    L.d_coef32 = A.alloc_n<float>((size_t)L.lay.nC * 15 * mq);
+    const size_t ncoef = (size_t)L.lay.nC * 15 * mq;
+    const size_t nline = (size_t)L.lay.nC * n_cell_lines(N) * line_rec(q);
+    if (s->q != q || !L.d_coef) {  // (re)allocate only when the degree changes
+      for (void* p : {(void*)L.d_coef, (void*)L.d_coef32, (void*)L.d_line64, (void*)L.d_cell_e}) A.release(p);
+      L.d_coef = A.alloc_n<double>(ncoef);
+      L.d_coef32 = A.alloc_n<float>(ncoef);
+      L.d_line64 = A.alloc_n<long long>(nline);
+      L.d_cell_e = A.alloc_n<int>((size_t)L.lay.nC);
+    }
     // sample in chunks of cells so the sample buffer stays below ~1 GB
     const int64_t per_cell = (int64_t)np * 14;
     const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(L.lay.nC, (int64_t)(1 << 27) / per_cell));
@@ -527,6 +558,7 @@ static void fit(hhg_shell* s, int q, int j, cudaStream_t st) {
       launch_fit_coef(nc, mq, np, d_P, d_sc, d_b, L.d_coef + (int64_t)c0 * 15 * mq, L.d_coef32 + (int64_t)c0 * 15 * mq,
                       st);
     }
+    launch_line_table(v, q, L.d_coef, L.d_cell_e, L.d_line64, st);
     HHG_CUDA(cudaStreamSynchronize(st));
     A.release(d_b);
     A.release(d_pts);
@@ -639,7 +671,7 @@ hhg_status hhg_timing_read(hhg_shell* s, int which, double* total_ms, int64_t* l
       tot += ms;
     }
     if (total_ms) *total_ms = tot;
-    if (launches) *launches = (int64_t)s->tevents[which].size();
+    if (launches) *launches = which == HHG_T_COARSE ? s->cg_iters : (int64_t)s->tevents[which].size();
   });
 }
 

@@ -1,19 +1,29 @@
 // Cell-interior kernels: the volume primitives, which hold all but
 // O(2^{2l}) of the nodes (Sec. 2.3).
 //
-// One CTA per macro cell walks the planes k = 1 .. N-3 of the cell.  For the
-// surrogate (LSQP, Sec. 3.4), the 3-variate polynomial of every direction is
-// reduced once per line (j, k) to a polynomial in i -- the line-wise
-// evaluation the paper builds on (Sec. 3.4; Eq. 5.4) -- and kept in shared
-// memory; each node then needs q multiply-adds per weight.  For IFEM
-// (Sec. 4.2.1) every node assembles its 15 weights from the 24 element
-// matrices around it.
+// Surrogate (LSQP, Sec. 3.4).  For a fixed line (j, k) each of the 15
+// 3-variate polynomials is a polynomial of degree q in i -- the line-wise
+// evaluation the paper builds on (Sec. 3.4; Eq. 5.4).  Two designs, one per
+// precision, because GB300 issues FP64 at a small fraction of its FP32 and
+// INT32 rate:
 //
-// The smoother (Eq. 5.1) runs the four colours (i + 2j + 3k) mod 4 of the
-// cell in one launch: in step s the CTA updates colour c on plane s + 1 - c,
-// c = 0..3, in that order, with a barrier after each colour.  Every update of
-// colour c then sees all colour < c updates of its neighbours (planes k - 1,
-// k, k + 1) and none of colour > c, exactly as four separate colour sweeps.
+//  * FP64: the line polynomials of every cell are computed once per fit
+//    (lsqp_line_table_kernel) as integers scaled by 2^E (E per cell, chosen so
+//    every partial sum stays below 2^62) and kept in HBM.  Per node the
+//    polynomial is evaluated exactly by integer Horner and converted to FP64
+//    once per weight; the FP64 pipe then only carries the conversions, the 14
+//    stencil products and the divide.  Kernels are thread-per-node with one
+//    CTA per macro cell and no barriers; the smoother is one launch per colour.
+//  * FP32: one CTA per cell walks its planes; the line coefficients of a plane
+//    are computed in shared memory (FP32 arithmetic is cheap, HBM traffic is
+//    the bound), and the four colours run in one launch as a plane wavefront:
+//    in step s colour c is updated on plane s + 1 - c, c = 0..3, with a
+//    barrier after each colour, so every update sees all lower-colour updates
+//    of planes k - 1, k, k + 1 and none of the higher ones -- exactly four
+//    colour sweeps in one pass over the cell.
+//
+// IFEM (Sec. 4.2.1): every node assembles its 15 weights from the 24 element
+// matrices around it (thread per node, one launch per colour).
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -23,7 +33,8 @@ namespace hhg {
 
 namespace {
 
-constexpr int CELL_THREADS = 128;
+constexpr int WAVE_THREADS = 128;  // FP32 wavefront kernel
+constexpr int NODE_THREADS = 256;  // thread-per-node kernels
 
 // Coefficients of the polynomial in i along line (j, k): c_a(j, k) =
 // sum_{b,d} A_{a,b,d} j^b k^d.  Storage order of A (per direction):
@@ -58,33 +69,126 @@ __device__ __forceinline__ T eval_line(const T* cl, T i) {
   return v;
 }
 
-// Stencil application at one interior node from its 15 weights.
+// Stencil application at one interior node from its 15 weights (sw may be
+// scaled by 2^E; `scale` = 2^E, `inv_scale` = 2^-E, 1 when unscaled).
 template <class T, Mode MODE>
 __device__ __forceinline__ void node_update(const LevelView<T>& lv, int c, int i, int j, int k, const T* sw,
-                                            T* u, T* out, const T* f, double& nrm) {
+                                            T* u, T* out, const T* f, double& nrm, T scale, T inv_scale) {
   const int64_t I = lv.off_C + (int64_t)c * lv.n_int + lin_interior(i, j, k, lv.N);
+  const T* uc = u;
   if (MODE == SMOOTH) {
-    T acc = f[I];
+    T a0 = f[I] * scale, a1 = 0;
 #pragma unroll
-    for (int w = 0; w < 14; ++w) acc = fma(-sw[w], load_pt(lv, (const T*)u, c, i + DI(w), j + DJ(w), k + DK(w)), acc);
-    u[I] = acc / sw[MC];
-  } else if (MODE == APPLY) {
-    T acc = sw[MC] * u[I];
-#pragma unroll
-    for (int w = 0; w < 14; ++w) acc = fma(sw[w], load_pt(lv, (const T*)u, c, i + DI(w), j + DJ(w), k + DK(w)), acc);
-    out[I] = acc;
+    for (int w = 0; w < 14; w += 2) {
+      a0 = fma(-sw[w], load_pt(lv, uc, c, i + DI(w), j + DJ(w), k + DK(w)), a0);
+      a1 = fma(-sw[w + 1], load_pt(lv, uc, c, i + DI(w + 1), j + DJ(w + 1), k + DK(w + 1)), a1);
+    }
+    u[I] = (a0 + a1) / sw[MC];
   } else {
-    T acc = fma(-sw[MC], u[I], f[I]);
+    T a0 = sw[MC] * u[I], a1 = 0;
 #pragma unroll
-    for (int w = 0; w < 14; ++w) acc = fma(-sw[w], load_pt(lv, (const T*)u, c, i + DI(w), j + DJ(w), k + DK(w)), acc);
-    out[I] = acc;
-    nrm += (double)acc * (double)acc;
+    for (int w = 0; w < 14; w += 2) {
+      a0 = fma(sw[w], load_pt(lv, uc, c, i + DI(w), j + DJ(w), k + DK(w)), a0);
+      a1 = fma(sw[w + 1], load_pt(lv, uc, c, i + DI(w + 1), j + DJ(w + 1), k + DK(w + 1)), a1);
+    }
+    const T y = a0 + a1;
+    if (MODE == APPLY) {
+      out[I] = y * inv_scale;
+    } else {
+      const T r = fma(-inv_scale, y, f[I]);
+      out[I] = r;
+      nrm += (double)r * (double)r;
+    }
   }
 }
 
-template <class T, int Q, Mode MODE>
-__global__ void __launch_bounds__(CELL_THREADS) lsqp_cell_kernel(LevelView<T> lv, T* u, T* out, const T* f,
+// ---------------------------------------------------------------------------
+// FP64 surrogate: line table at fit time, thread-per-node application
+// ---------------------------------------------------------------------------
+
+// E per cell: B = max_w sum_t |A_wt| N^deg(t) bounds |c_a(j,k)| i^a on every
+// line and node, so with B 2^E < 2^60 every Horner partial sum of
+// C_q i^q + .. + C_0 stays below (q + 1) 2^60 <= 2^62.
+template <int Q>
+__global__ void lsqp_scale_kernel(const double* __restrict__ coef, int nC, int N, int* __restrict__ cell_e) {
+  constexpr int MQ = (Q + 1) * (Q + 2) * (Q + 3) / 6;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nC) return;
+  const int L = 31 - __clz(N);
+  double B = 0.0;
+  for (int w = 0; w < 15; ++w) {
+    double s = 0.0;
+    int t = 0;
+    for (int a = 0; a <= Q; ++a)
+      for (int d = 0; d <= Q - a; ++d)
+        for (int b = 0; b <= Q - a - d; ++b, ++t)
+          s += fabs(coef[((int64_t)c * 15 + w) * MQ + t]) * ldexp(1.0, (a + b + d) * L);
+    B = fmax(B, s);
+  }
+  cell_e[c] = 60 - (ilogb(B > 0.0 ? B : 1.0) + 1);
+}
+
+template <int Q>
+__global__ void lsqp_line_table_kernel(const double* __restrict__ coef, const int* __restrict__ cell_e, int nC, int N,
+                                       long long* __restrict__ table) {
+  constexpr int MQ = (Q + 1) * (Q + 2) * (Q + 3) / 6;
+  const int nl = (int)n_cell_lines(N);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nC * nl) return;
+  const int c = (int)(t / nl), line = (int)(t % nl);
+  int k = 1, j = line + 1;
+  while (j > N - 2 - k) {
+    j -= N - 2 - k;
+    ++k;
+  }
+  const double sc = ldexp(1.0, cell_e[c]);
+  long long* dst = table + t * line_rec(Q);
+  for (int w = 0; w < 15; ++w) {
+    double cl[Q + 1];
+    line_coeffs<double, Q>(coef + ((int64_t)c * 15 + w) * MQ, (double)j, (double)k, cl);
+#pragma unroll
+    for (int a = 0; a <= Q; ++a) dst[w * (Q + 1) + a] = __double2ll_rn(cl[a] * sc);
+  }
+  for (int r = 15 * (Q + 1); r < line_rec(Q); ++r) dst[r] = 0;
+}
+
+template <int Q, Mode MODE>
+__global__ void __launch_bounds__(NODE_THREADS) lsqp_node_kernel(LevelView<double> lv, const uint32_t* __restrict__ list,
+                                                                  int n_list, double* u, double* out, const double* f,
                                                                   double* partial) {
+  const int c = blockIdx.x;
+  const int N = lv.N;
+  const int E = lv.cell_e[c];
+  const double scale = ldexp(1.0, E), inv_scale = ldexp(1.0, -E);
+  const long long* tab = lv.line64 + (int64_t)c * lv.n_lines * line_rec(Q);
+  double nrm = 0.0;
+  for (int t = threadIdx.x; t < n_list; t += blockDim.x) {
+    const uint32_t p = list[t];
+    const int i = unpack_i(p), j = unpack_j(p), k = unpack_k(p);
+    const long long* C = tab + (int64_t)line_id(j, k, N) * line_rec(Q);
+    double sw[15];
+#pragma unroll
+    for (int w = 0; w < 15; ++w) {
+      long long v = C[w * (Q + 1) + Q];
+#pragma unroll
+      for (int a = Q - 1; a >= 0; --a) v = v * (long long)i + C[w * (Q + 1) + a];
+      sw[w] = (double)v;
+    }
+    node_update<double, MODE>(lv, c, i, j, k, sw, u, out, f, nrm, scale, inv_scale);
+  }
+  if (MODE == RESIDUAL) {
+    const double tot = block_sum(nrm);
+    if (threadIdx.x == 0) partial[c] = tot;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 surrogate: plane wavefront with shared-memory line coefficients
+// ---------------------------------------------------------------------------
+
+template <class T, int Q, Mode MODE>
+__global__ void __launch_bounds__(WAVE_THREADS) lsqp_wave_kernel(LevelView<T> lv, T* u, T* out, const T* f,
+                                                                 double* partial) {
   constexpr int MQ = (Q + 1) * (Q + 2) * (Q + 3) / 6;
   constexpr int NSLOT = (MODE == SMOOTH) ? 4 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -114,7 +218,7 @@ __global__ void __launch_bounds__(CELL_THREADS) lsqp_cell_kernel(LevelView<T> lv
       T sw[15];
 #pragma unroll
       for (int w = 0; w < 15; ++w) sw[w] = eval_line<T, Q>(cl + w * (Q + 1), (T)i);
-      node_update<T, MODE>(lv, c, i, j, k, sw, u, out, f, nrm);
+      node_update<T, MODE>(lv, c, i, j, k, sw, u, out, f, nrm, T(1), T(1));
     }
   };
 
@@ -143,153 +247,29 @@ __global__ void __launch_bounds__(CELL_THREADS) lsqp_cell_kernel(LevelView<T> lv
   }
 }
 
-// FP64 surrogate kernel with the weights evaluated in exact 64-bit integer
-// arithmetic.  GB300 issues FP64 at a small fraction of its FP32/INT32 rate,
-// and evaluating the 15 line polynomials is half of the FP64 work of an
-// update.  Here the line coefficients are scaled by 2^E (E per cell, chosen
-// so that every partial sum stays below 2^62) and rounded to integers once
-// per line; per node the polynomial is evaluated by integer Horner (exact) and
-// converted to FP64 once per weight.  The weights equal the FP64 ones to the
-// rounding of the conversion; the factor 2^-E is applied once per node.
-__device__ __forceinline__ long long horner_i64(const long long* C, int i, int Q) {
-  long long v = C[Q];
-  for (int a = Q - 1; a >= 0; --a) v = v * (long long)i + C[a];
-  return v;
-}
-
-template <int Q, Mode MODE, int THREADS>
-__global__ void __launch_bounds__(THREADS) lsqp_cell_kernel_iw(LevelView<double> lv, double* u, double* out,
-                                                                const double* f, double* partial) {
-  constexpr int MQ = (Q + 1) * (Q + 2) * (Q + 3) / 6;
-  constexpr int NSLOT = (MODE == SMOOTH) ? 4 : 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* sA = reinterpret_cast<double*>(smem_raw);          // [15][MQ]
-  long long* ring = reinterpret_cast<long long*>(sA + 15 * MQ);  // [NSLOT][NL][15][Q+1]
-  __shared__ double s_bound[THREADS / 32];
-  const int c = blockIdx.x;
-  const int N = lv.N;
-  const int NL = N - 3;
-  for (int t = threadIdx.x; t < 15 * MQ; t += blockDim.x) sA[t] = lv.coef[(int64_t)c * 15 * MQ + t];
-  __syncthreads();
-  // B = max_w sum_t |A_wt| N^deg(t) bounds |c_a(j,k)| i^a for every line and node
-  double bnd = 0.0;
-  if (threadIdx.x < 15) {
-    int t = 0;
-    for (int a = 0; a <= Q; ++a)
-      for (int d = 0; d <= Q - a; ++d)
-        for (int b = 0; b <= Q - a - d; ++b, ++t)
-          bnd += fabs(sA[threadIdx.x * MQ + t]) * ldexp(1.0, (a + b + d) * (31 - __clz(N)));  // N = 2^L
-  }
-  for (int o = 16; o > 0; o >>= 1) bnd = fmax(bnd, __shfl_down_sync(0xffffffffu, bnd, o));
-  if ((threadIdx.x & 31) == 0) s_bound[threadIdx.x >> 5] = bnd;
-  __syncthreads();
-  double B = 0.0;
-  for (int w = 0; w < THREADS / 32; ++w) B = fmax(B, s_bound[w]);
-  const int ex = ilogb(B > 0.0 ? B : 1.0) + 1;  // B < 2^ex
-  const int E = 60 - ex;          // B 2^E < 2^60: |C2 i^2 + C1 i + C0| < 3 * 2^60
-  const double scale = ldexp(1.0, E), inv_scale = ldexp(1.0, -E);
-  double nrm = 0.0;
-
-  auto prologue = [&](int k) {
-    const int slot = (NSLOT == 4) ? (k & 3) : 0;
-    for (int jj = threadIdx.x; jj < N - 2 - k; jj += blockDim.x) {
-      long long* dst = ring + ((slot * NL + jj) * 15) * (Q + 1);
-#pragma unroll 1
-      for (int w = 0; w < 15; ++w) {
-        double cl[Q + 1];
-        line_coeffs<double, Q>(sA + w * MQ, (double)(jj + 1), (double)k, cl);
-#pragma unroll
-        for (int a = 0; a <= Q; ++a) dst[w * (Q + 1) + a] = __double2ll_rn(cl[a] * scale);
-      }
-    }
-  };
-  auto process = [&](int k, int beg, int end) {
-    const int slot = (NSLOT == 4) ? (k & 3) : 0;
-    for (int t = beg + threadIdx.x; t < end; t += blockDim.x) {
-      const uint32_t p = lv.plane_nodes[t];
-      const int i = unpack_i(p), j = unpack_j(p);
-      const long long* cl = ring + ((slot * NL + (j - 1)) * 15) * (Q + 1);
-      double sw[15];
-#pragma unroll
-      for (int w = 0; w < 15; ++w) sw[w] = (double)horner_i64(cl + w * (Q + 1), i, Q);
-      const int64_t I = lv.off_C + (int64_t)c * lv.n_int + lin_interior(i, j, k, N);
-      if (MODE == SMOOTH) {
-        double acc = f[I] * scale;
-#pragma unroll
-        for (int w = 0; w < 14; ++w) acc = fma(-sw[w], load_pt(lv, (const double*)u, c, i + DI(w), j + DJ(w), k + DK(w)), acc);
-        u[I] = acc / sw[MC];
-      } else {
-        double acc = sw[MC] * u[I];
-#pragma unroll
-        for (int w = 0; w < 14; ++w) acc = fma(sw[w], load_pt(lv, (const double*)u, c, i + DI(w), j + DJ(w), k + DK(w)), acc);
-        if (MODE == APPLY) {
-          out[I] = acc * inv_scale;
-        } else {
-          const double r = fma(-inv_scale, acc, f[I]);
-          out[I] = r;
-          nrm += r * r;
-        }
-      }
-    }
-  };
-
-  if (MODE == SMOOTH) {
-    for (int s = 0; s <= N - 1; ++s) {
-      if (s + 1 <= N - 3) prologue(s + 1);
-      __syncthreads();
-#pragma unroll 1
-      for (int cc = 0; cc < 4; ++cc) {
-        const int k = s + 1 - cc;
-        if (k >= 1 && k <= N - 3) process(k, lv.plane_off[k * 4 + cc], lv.plane_off[k * 4 + cc + 1]);
-        __syncthreads();
-      }
-    }
-  } else {
-    for (int k = 1; k <= N - 3; ++k) {
-      prologue(k);
-      __syncthreads();
-      process(k, lv.plane_off[k * 4], lv.plane_off[k * 4 + 4]);
-      __syncthreads();
-    }
-  }
-  if (MODE == RESIDUAL) {
-    const double tot = block_sum(nrm);
-    if (threadIdx.x == 0) partial[c] = tot;
-  }
-}
+// ---------------------------------------------------------------------------
+// IFEM: exact stencils assembled on the fly, thread per node
+// ---------------------------------------------------------------------------
 
 template <class T, Mode MODE>
-__global__ void __launch_bounds__(CELL_THREADS) ifem_cell_kernel(LevelView<T> lv, T* u, T* out, const T* f,
+__global__ void __launch_bounds__(NODE_THREADS) ifem_node_kernel(LevelView<T> lv, const uint32_t* __restrict__ list,
+                                                                  int n_list, T* u, T* out, const T* f,
                                                                   double* partial) {
   __shared__ CellGeom g;
   const int c = blockIdx.x;
-  const int N = lv.N;
-  if (threadIdx.x < 16) reinterpret_cast<double*>(&g)[threadIdx.x] = reinterpret_cast<const double*>(&lv.geom[c])[threadIdx.x];
+  if (threadIdx.x < 16)
+    reinterpret_cast<double*>(&g)[threadIdx.x] = reinterpret_cast<const double*>(&lv.geom[c])[threadIdx.x];
   __syncthreads();
   double nrm = 0.0;
-  auto process = [&](int k, int beg, int end) {
-    for (int t = beg + threadIdx.x; t < end; t += blockDim.x) {
-      const uint32_t p = lv.plane_nodes[t];
-      const int i = unpack_i(p), j = unpack_j(p);
-      double s[15];
-      ifem_stencil(g, N, i, j, k, s);
-      T sw[15];
+  for (int t = threadIdx.x; t < n_list; t += blockDim.x) {
+    const uint32_t p = list[t];
+    const int i = unpack_i(p), j = unpack_j(p), k = unpack_k(p);
+    double s[15];
+    ifem_stencil(g, lv.N, i, j, k, s);
+    T sw[15];
 #pragma unroll
-      for (int w = 0; w < 15; ++w) sw[w] = (T)s[w];
-      node_update<T, MODE>(lv, c, i, j, k, sw, u, out, f, nrm);
-    }
-  };
-  if (MODE == SMOOTH) {
-    for (int s = 0; s <= N - 1; ++s) {
-#pragma unroll 1
-      for (int cc = 0; cc < 4; ++cc) {
-        const int k = s + 1 - cc;
-        if (k >= 1 && k <= N - 3) process(k, lv.plane_off[k * 4 + cc], lv.plane_off[k * 4 + cc + 1]);
-        __syncthreads();
-      }
-    }
-  } else {
-    for (int k = 1; k <= N - 3; ++k) process(k, lv.plane_off[k * 4], lv.plane_off[k * 4 + 4]);
+    for (int w = 0; w < 15; ++w) sw[w] = (T)s[w];
+    node_update<T, MODE>(lv, c, i, j, k, sw, u, out, f, nrm, T(1), T(1));
   }
   if (MODE == RESIDUAL) {
     const double tot = block_sum(nrm);
@@ -297,33 +277,73 @@ __global__ void __launch_bounds__(CELL_THREADS) ifem_cell_kernel(LevelView<T> lv
   }
 }
 
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
 template <class T, int Q, Mode MODE>
-void launch_lsqp(const LevelView<T>& lv, T* u, T* out, const T* f, double* partial, cudaStream_t st) {
+void launch_wave(const LevelView<T>& lv, T* u, T* out, const T* f, double* partial, cudaStream_t st) {
   constexpr int MQ = (Q + 1) * (Q + 2) * (Q + 3) / 6;
   constexpr int NSLOT = (MODE == SMOOTH) ? 4 : 1;
   const size_t smem = sizeof(T) * (15 * MQ + (size_t)NSLOT * (lv.N - 3) * 15 * (Q + 1));
-  if constexpr (sizeof(T) == 8) {
-    auto k2 = lsqp_cell_kernel_iw<Q, MODE, 256>;
-    if (smem > 48 * 1024) HHG_CUDA(cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k2<<<lv.nC, 256, smem, st>>>(lv, u, out, f, partial);
-    HHG_CUDA(cudaGetLastError());
-    count_launch();
-    return;
-  }
-  auto kern = lsqp_cell_kernel<T, Q, MODE>;
+  auto kern = lsqp_wave_kernel<T, Q, MODE>;
   if (smem > 48 * 1024) HHG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<lv.nC, CELL_THREADS, smem, st>>>(lv, u, out, f, partial);
+  kern<<<lv.nC, WAVE_THREADS, smem, st>>>(lv, u, out, f, partial);
   HHG_CUDA(cudaGetLastError());
   count_launch();
 }
 
+template <int Q, Mode MODE>
+void launch_node64(const LevelView<double>& lv, const uint32_t* list, int n, double* u, double* out, const double* f,
+                   double* partial, cudaStream_t st) {
+  HHG_CHECK(lv.line64 != nullptr, HHG_ENOTFIT, "FP64 surrogate line table missing");
+  lsqp_node_kernel<Q, MODE><<<lv.nC, NODE_THREADS, 0, st>>>(lv, list, n, u, out, f, partial);
+  HHG_CUDA(cudaGetLastError());
+  count_launch();
+}
+
+template <int Q>
+void lsqp64(const LevelView<double>& lv, Mode mode, double* u, double* out, const double* f, double* partial,
+            cudaStream_t st) {
+  switch (mode) {
+    case APPLY: launch_node64<Q, APPLY>(lv, lv.int_ijk, (int)lv.n_int, u, out, f, partial, st); break;
+    case RESIDUAL: launch_node64<Q, RESIDUAL>(lv, lv.int_ijk, (int)lv.n_int, u, out, f, partial, st); break;
+    case SMOOTH:
+      for (int cc = 0; cc < 4; ++cc)
+        launch_node64<Q, SMOOTH>(lv, lv.colour_nodes + lv.colour_off[cc], lv.colour_off[cc + 1] - lv.colour_off[cc],
+                                 u, out, f, partial, st);
+      break;
+  }
+}
+
 template <class T, Mode MODE>
-void dispatch_q(const LevelView<T>& lv, T* u, T* out, const T* f, double* partial, cudaStream_t st) {
+void dispatch_wave(const LevelView<T>& lv, T* u, T* out, const T* f, double* partial, cudaStream_t st) {
   switch (lv.q) {
-    case 1: launch_lsqp<T, 1, MODE>(lv, u, out, f, partial, st); break;
-    case 2: launch_lsqp<T, 2, MODE>(lv, u, out, f, partial, st); break;
-    case 3: launch_lsqp<T, 3, MODE>(lv, u, out, f, partial, st); break;
+    case 1: launch_wave<T, 1, MODE>(lv, u, out, f, partial, st); break;
+    case 2: launch_wave<T, 2, MODE>(lv, u, out, f, partial, st); break;
+    case 3: launch_wave<T, 3, MODE>(lv, u, out, f, partial, st); break;
     default: throw Error{HHG_ENOTFIT, "surrogate degree not fitted"};
+  }
+}
+
+template <class T, Mode MODE>
+void launch_ifem(const LevelView<T>& lv, const uint32_t* list, int n, T* u, T* out, const T* f, double* partial,
+                 cudaStream_t st) {
+  ifem_node_kernel<T, MODE><<<lv.nC, NODE_THREADS, 0, st>>>(lv, list, n, u, out, f, partial);
+  HHG_CUDA(cudaGetLastError());
+  count_launch();
+}
+
+template <class T>
+void ifem_all(const LevelView<T>& lv, Mode mode, T* u, T* out, const T* f, double* partial, cudaStream_t st) {
+  switch (mode) {
+    case APPLY: launch_ifem<T, APPLY>(lv, lv.int_ijk, (int)lv.n_int, u, out, f, partial, st); break;
+    case RESIDUAL: launch_ifem<T, RESIDUAL>(lv, lv.int_ijk, (int)lv.n_int, u, out, f, partial, st); break;
+    case SMOOTH:
+      for (int cc = 0; cc < 4; ++cc)
+        launch_ifem<T, SMOOTH>(lv, lv.colour_nodes + lv.colour_off[cc], lv.colour_off[cc + 1] - lv.colour_off[cc], u,
+                               out, f, partial, st);
+      break;
   }
 }
 
@@ -373,31 +393,60 @@ __global__ void fit_coef_kernel(int nC, int mq, int n_pts, const double* __restr
 
 }  // namespace
 
-template <class T>
-void launch_cell(const LevelView<T>& lv, int op, Mode mode, T* u, T* out, const T* f, double* partial,
-                 cudaStream_t st) {
+template <>
+void launch_cell<double>(const LevelView<double>& lv, int op, Mode mode, double* u, double* out, const double* f,
+                         double* partial, cudaStream_t st) {
   if (lv.N < 4 || lv.n_int == 0) return;
   if (op == HHG_OP_LSQP && lv.q > 0) {
-    switch (mode) {
-      case APPLY: dispatch_q<T, APPLY>(lv, u, out, f, partial, st); break;
-      case RESIDUAL: dispatch_q<T, RESIDUAL>(lv, u, out, f, partial, st); break;
-      case SMOOTH: dispatch_q<T, SMOOTH>(lv, u, out, f, partial, st); break;
+    switch (lv.q) {
+      case 1: lsqp64<1>(lv, mode, u, out, f, partial, st); break;
+      case 2: lsqp64<2>(lv, mode, u, out, f, partial, st); break;
+      case 3: lsqp64<3>(lv, mode, u, out, f, partial, st); break;
+      default: throw Error{HHG_ENOTFIT, "surrogate degree not fitted"};
     }
     return;
   }
-  switch (mode) {
-    case APPLY: ifem_cell_kernel<T, APPLY><<<lv.nC, CELL_THREADS, 0, st>>>(lv, u, out, f, partial); break;
-    case RESIDUAL: ifem_cell_kernel<T, RESIDUAL><<<lv.nC, CELL_THREADS, 0, st>>>(lv, u, out, f, partial); break;
-    case SMOOTH: ifem_cell_kernel<T, SMOOTH><<<lv.nC, CELL_THREADS, 0, st>>>(lv, u, out, f, partial); break;
-  }
-  HHG_CUDA(cudaGetLastError());
-  count_launch();
+  ifem_all<double>(lv, mode, u, out, f, partial, st);
 }
 
-template void launch_cell<double>(const LevelView<double>&, int, Mode, double*, double*, const double*, double*,
-                                  cudaStream_t);
-template void launch_cell<float>(const LevelView<float>&, int, Mode, float*, float*, const float*, double*,
-                                 cudaStream_t);
+template <>
+void launch_cell<float>(const LevelView<float>& lv, int op, Mode mode, float* u, float* out, const float* f,
+                        double* partial, cudaStream_t st) {
+  if (lv.N < 4 || lv.n_int == 0) return;
+  if (op == HHG_OP_LSQP && lv.q > 0) {
+    switch (mode) {
+      case APPLY: dispatch_wave<float, APPLY>(lv, u, out, f, partial, st); break;
+      case RESIDUAL: dispatch_wave<float, RESIDUAL>(lv, u, out, f, partial, st); break;
+      case SMOOTH: dispatch_wave<float, SMOOTH>(lv, u, out, f, partial, st); break;
+    }
+    return;
+  }
+  ifem_all<float>(lv, mode, u, out, f, partial, st);
+}
+
+void launch_line_table(const LevelView<double>& lv, int q, const double* coef, int* cell_e, long long* table,
+                       cudaStream_t st) {
+  const int64_t n = (int64_t)lv.nC * n_cell_lines(lv.N);
+  const unsigned gs = (unsigned)((lv.nC + 127) / 128), gl = (unsigned)((n + 127) / 128);
+  switch (q) {
+    case 1:
+      lsqp_scale_kernel<1><<<gs, 128, 0, st>>>(coef, lv.nC, lv.N, cell_e);
+      lsqp_line_table_kernel<1><<<gl, 128, 0, st>>>(coef, cell_e, lv.nC, lv.N, table);
+      break;
+    case 2:
+      lsqp_scale_kernel<2><<<gs, 128, 0, st>>>(coef, lv.nC, lv.N, cell_e);
+      lsqp_line_table_kernel<2><<<gl, 128, 0, st>>>(coef, cell_e, lv.nC, lv.N, table);
+      break;
+    case 3:
+      lsqp_scale_kernel<3><<<gs, 128, 0, st>>>(coef, lv.nC, lv.N, cell_e);
+      lsqp_line_table_kernel<3><<<gl, 128, 0, st>>>(coef, cell_e, lv.nC, lv.N, table);
+      break;
+    default:
+      throw Error{HHG_EINVAL, "q must be 1, 2 or 3"};
+  }
+  HHG_CUDA(cudaGetLastError());
+  count_launch(2);
+}
 
 void launch_sample(const LevelView<double>& lv, const uint32_t* pts, int n_pts, double* b, cudaStream_t st) {
   const int64_t n = (int64_t)lv.nC * n_pts;

@@ -12,17 +12,28 @@ namespace hhg {
 enum Mode { APPLY = 0, RESIDUAL = 1, SMOOTH = 2 };
 
 // ---- cell interiors (cell.cu) ----------------------------------------------
-// One CTA per macro cell walks its planes k = 1 .. N-3.
+// One CTA per macro cell (grid = nC).
 //   APPLY:    out = L u on the interior nodes
-//   RESIDUAL: out = f - L u, partial[c] = sum of out^2 over cell c
+//   RESIDUAL: out = f - L u, partial[c] = sum of out^2 over cell c (nC slots)
 //   SMOOTH:   the four colour steps (i + 2j + 3k) mod 4 = 0..3 of Eq. 5.1,
-//             u updated in place, in a plane wavefront (colour c at plane
-//             s + 1 - c in step s), which orders every update after all
-//             lower-colour updates of its neighbours.
+//             u updated in place (FP64: one launch per colour; FP32: one
+//             plane-wavefront launch).
 // op: 0 = IFEM (on-the-fly exact stencils), 1 = LSQP (surrogate).
 template <class T>
 void launch_cell(const LevelView<T>& lv, int op, Mode mode, T* u, T* out, const T* f, double* partial,
                  cudaStream_t st);
+template <>
+void launch_cell<double>(const LevelView<double>& lv, int op, Mode mode, double* u, double* out, const double* f,
+                         double* partial, cudaStream_t st);
+template <>
+void launch_cell<float>(const LevelView<float>& lv, int op, Mode mode, float* u, float* out, const float* f,
+                        double* partial, cudaStream_t st);
+
+// FP64 surrogate line table (fit time): per cell the scale exponent E and,
+// per line (j, k), the q+1 coefficients of each of the 15 polynomials in i,
+// times 2^E, rounded to int64.
+void launch_line_table(const LevelView<double>& lv, int q, const double* coef, int* cell_e, long long* table,
+                       cudaStream_t st);
 
 // Exact stencils (14 off-centre weights) at cell-local points of every cell:
 // b[(c * n_pts + p) * 14 + w] (Table 4.3 "t_sample").

@@ -54,6 +54,13 @@ struct LevelView {
   T* ghost;                      // [nC * n_full] per-cell copies of boundary values
   const T* coef;                 // [nC * 15 * m_q] surrogate coefficients (raw index monomials)
   int q;                         // surrogate degree (0 = not fitted)
+  // FP64 surrogate: per cell and line (j, k), the 15 polynomials in i as
+  // integers scaled by 2^cell_e[c] (records of line_rec(q) int64)
+  const long long* line64;
+  const int* cell_e;             // [nC]
+  int n_lines;                   // lines per cell, (N - 3)(N - 2) / 2
+  const uint32_t* colour_nodes;  // interior points (packed) ordered (colour, k, j, i)
+  int colour_off[5];             // start of each colour in colour_nodes
   // lower primitives: canonical rows 0 .. off_C-1 in sliced ELL (32-row
   // slices, column-major inside a slice), Dirichlet rows have diag 0
   const int64_t* sell_ptr;       // [n_slices + 1]
@@ -94,6 +101,10 @@ struct Level {
   // surrogate
   double* d_coef = nullptr;
   float* d_coef32 = nullptr;
+  long long* d_line64 = nullptr;
+  int* d_cell_e = nullptr;
+  uint32_t* d_colour_nodes = nullptr;
+  int colour_off[5] = {0, 0, 0, 0, 0};
   // halo copies and work vectors (allocated on demand)
   double* d_ghost64 = nullptr;
   float* d_ghost32 = nullptr;
@@ -105,6 +116,14 @@ struct Level {
 
 // Number of monomials of total degree <= q in three variables (Eq. 3.2).
 HD int n_coeffs(int q) { return (q + 1) * (q + 2) * (q + 3) / 6; }
+
+// int64 per line record of the FP64 surrogate: 15 (q + 1) rounded up to a
+// multiple of 16 (128-byte aligned records).
+HD int line_rec(int q) { return (15 * (q + 1) + 15) / 16 * 16; }
+
+// Lines (j, k) of a cell's interior, k = 1..N-3, j = 1..N-2-k, in (k, j) order.
+HD int64_t n_cell_lines(int N) { return (int64_t)(N - 3) * (N - 2) / 2; }
+HD int line_id(int j, int k, int N) { return (k - 1) * (N - 2) - k * (k - 1) / 2 + (j - 1); }
 
 }  // namespace hhg
 
@@ -124,6 +143,7 @@ struct hhg_shell {
   // diagnostics: CUDA-event pairs around timed kernel launches
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tevents[HHG_T_COUNT];
+  int64_t cg_iters = 0;
 
   hhg::Level& level_of(int L) { return levels.at(L - 2); }
 };
