@@ -416,54 +416,28 @@ static double read_scalar(hhg_shell* s, int slot, cudaStream_t st) {
 }
 
 // Coarsest level (N = 4): Jacobi-preconditioned conjugate gradients on the
-// exact, symmetric operator, to ||r|| <= 1e-13 ||f|| (the paper uses
-// Gauss-Seidel as coarse solver, Sec. 4; an exact solve keeps the cycle
-// independent of that choice).
+// exact, symmetric operator, pre-assembled at setup (coarse.cu), to
+// ||r|| <= 1e-13 ||f|| (the paper uses Gauss-Seidel as coarse solver, Sec. 4;
+// an exact solve keeps the cycle independent of that choice).
 static void coarse_solve(hhg_shell* s, const double* f, double* x, cudaStream_t st) {
   TimedScope all(s, -1, HHG_T_COARSE, st);
-  Level& L = s->levels[0];
-  const int64_t n = L.lay.n_total;
+  const CoarseOp& A = *static_cast<CoarseOp*>(s->coarse_op);
+  const int64_t n = A.n_total;
   double* r = s->d_cg;
   double* z = r + n;
   double* p = z + n;
   double* q = p + n;
-  double* dinv = q + n;
-  LevelView<double> v = view<double>(s, 0);
-  launch_coarse_diag(v, dinv, st);
-  HHG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
-  HHG_CUDA(cudaMemcpyAsync(r, f, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-  launch_zero_list(L.d_dirichlet, L.n_dirichlet, r, st);
-  const int nb = dot_blocks(n);
   double* part = s->d_red + 64;
-  enum { RZ = 0, PQ = 1, RZN = 2, RR = 3, FF = 4 };
-  auto dot = [&](const double* a, const double* b, int slot) {
-    launch_dot_partial(a, b, n, part, nb, st);
-    launch_sum(part, nb, s->d_red + slot, st);
-  };
-  dot(r, r, FF);
-  const double ff = read_scalar(s, FF, st);
+  // scalar slots: 0, 1 = r.z (double-buffered), 2 = r.r, 3 = r0.r0
+  launch_cg_init(A, f, x, r, z, p, part, s->d_red + 0, s->d_red + 3, st);
+  const double ff = read_scalar(s, 3, st);
   if (ff == 0.0) return;
-  {
-    // z = D^-1 r via the update kernel with alpha = 0, then p = z
-    HHG_CUDA(cudaMemsetAsync(s->d_red + PQ, 0, sizeof(double), st));
-    HHG_CUDA(cudaMemsetAsync(q, 0, sizeof(double) * n, st));
-    HHG_CUDA(cudaMemsetAsync(p, 0, sizeof(double) * n, st));
-    launch_cg_update(x, r, z, p, q, dinv, s->d_red + PQ, s->d_red + FF, n, st);
-    HHG_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-  }
-  dot(r, z, RZ);
   const double tol2 = 1e-26 * ff;
   for (int it = 0; it < 20000; ++it) {
     ++s->cg_iters;
-    op_apply(s, 0, HHG_OP_IFEM, p, q, st);
-    dot(p, q, PQ);
-    launch_cg_update(x, r, z, p, q, dinv, s->d_red + RZ, s->d_red + PQ, n, st);
-    dot(r, z, RZN);
-    launch_cg_dir(p, z, s->d_red + RZN, s->d_red + RZ, n, st);
-    HHG_CUDA(cudaMemcpyAsync(s->d_red + RZ, s->d_red + RZN, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    launch_cg_iteration(A, x, r, z, p, q, part, s->d_red + (it & 1), s->d_red + ((it + 1) & 1), s->d_red + 2, st);
     if ((it & 7) == 7) {
-      dot(r, r, RR);
-      const double rr = read_scalar(s, RR, st);
+      const double rr = read_scalar(s, 2, st);
       if (!std::isfinite(rr)) throw Error{HHG_EDIVERGED, "coarse solve diverged"};
       if (rr <= tol2) return;
     }
@@ -704,16 +678,35 @@ hhg_status hhg_setup_shell(const hhg_shell_desc* d, void* stream, hhg_shell** ou
       s->d_geom = upload(s->alloc, geom, st);
       s->levels.resize(s->Lf - 1);
       for (int n = 0; n < (int)s->levels.size(); ++n) build_level(s, n, st);
-      int64_t red = 64;
-      for (auto& L : s->levels)
-        red = std::max<int64_t>(red, 64 + L.lay.nC + low_blocks(L.lay.off_C) + dot_blocks(L.lay.n_total));
+      // reduction scratch: 64 scalar slots, then partial sums (per-cell and
+      // per-block residual partials, or the coarse solver's 3 CG_BLOCKS)
+      int64_t red = 64 + 3 * CG_BLOCKS;
+      for (auto& L : s->levels) red = std::max<int64_t>(red, 64 + L.lay.nC + low_blocks(L.lay.off_C));
       s->red_len = red + 64;
       s->d_red = s->alloc.alloc_n<double>((size_t)s->red_len);
       HHG_CUDA(cudaMemsetAsync(s->d_red, 0, sizeof(double) * s->red_len, st));
-      s->d_cg = s->alloc.alloc_n<double>((size_t)(5 * s->levels[0].lay.n_total));
+      {
+        const Level& L0 = s->levels[0];
+        const int64_t n0 = L0.lay.n_total;
+        s->d_cg = s->alloc.alloc_n<double>((size_t)(5 * n0));
+        CoarseOp* A = new CoarseOp{};
+        s->coarse_op = A;
+        A->n_total = n0;
+        A->off_C = L0.lay.off_C;
+        A->nC = (int)L0.lay.nC;
+        A->sell_ptr = L0.d_sell_ptr;
+        A->sell_col = L0.d_sell_col;
+        A->sell_val = L0.d_sell_val;
+        A->low_diag = L0.d_low_diag;
+        int* col = s->alloc.alloc_n<int>((size_t)(14 * L0.lay.nC));
+        double* val = s->alloc.alloc_n<double>((size_t)(14 * L0.lay.nC));
+        double* diag = s->alloc.alloc_n<double>((size_t)L0.lay.nC);
+        launch_coarse_setup(view<double>(s, 0), *A, col, val, diag, s->d_cg + 4 * n0, st);
+      }
       HHG_CUDA(cudaStreamSynchronize(st));
     } catch (...) {
       s->alloc.release_all();
+      delete static_cast<CoarseOp*>(s->coarse_op);
       delete s;
       throw;
     }
@@ -726,6 +719,7 @@ hhg_status hhg_destroy(hhg_shell* s) {
     if (!s) return;
     cudaDeviceSynchronize();
     timing_clear(s);
+    delete static_cast<CoarseOp*>(s->coarse_op);
     s->alloc.release_all();
     delete s;
   });

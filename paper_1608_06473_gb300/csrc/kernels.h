@@ -70,20 +70,31 @@ void launch_restrict(const LevelView<T>& fine, const LevelView<T>& coarse, const
 // out[0] = sum of partial[0 .. n-1] (fixed order, one block).
 void launch_sum(const double* partial, int n, double* out, cudaStream_t st);
 
-// Coarse-solver vector kernels (FP64).
-void launch_dot_partial(const double* a, const double* b, int64_t n, double* partial, int nblk, cudaStream_t st);
-int dot_blocks(int64_t n);
-// x += alpha p ; r -= alpha q with alpha = num / den (device scalars), z = r / d where d != 0
-void launch_cg_update(double* x, double* r, double* z, const double* p, const double* q, const double* dinv,
-                      const double* num, const double* den, int64_t n, cudaStream_t st);
-// p = z + (num_new / num_old) p
-void launch_cg_dir(double* p, const double* z, const double* num_new, const double* num_old, int64_t n,
-                   cudaStream_t st);
-// d_inv[i] = 1 / diag(i) for free nodes of the coarsest level, 0 otherwise
-void launch_coarse_diag(const LevelView<double>& lv, double* dinv, cudaStream_t st);
-
 template <class T>
 void launch_copy_cast(const double* src, T* dst, int64_t n, cudaStream_t st);
+
+// ---- coarsest-level conjugate gradients (coarse.cu) -------------------------
+constexpr int CG_BLOCKS = 128;
+struct CoarseOp {                // exact operator of the N = 4 level
+  int64_t n_total, off_C;
+  int nC;
+  const int64_t* sell_ptr;       // lower-primitive rows (the level's sliced ELL)
+  const int* sell_col;
+  const double* sell_val;
+  const double* low_diag;
+  const int* int_col;            // [14 nC] interior row of each cell, -1 = Dirichlet column
+  const double* int_val;         // [14 nC]
+  const double* int_diag;        // [nC]
+  const double* dinv;            // [n_total] inverse diagonal, 0 on Dirichlet rows
+};
+// Assembles the interior rows and the inverse diagonal (setup).
+void launch_coarse_setup(const LevelView<double>& lv, CoarseOp& A, int* col, double* val, double* diag, double* dinv,
+                         cudaStream_t st);
+// part needs 3 CG_BLOCKS doubles.
+void launch_cg_init(const CoarseOp& A, const double* f, double* x, double* r, double* z, double* p, double* part,
+                    double* rz_out, double* rr_out, cudaStream_t st);
+void launch_cg_iteration(const CoarseOp& A, double* x, double* r, double* z, double* p, double* q, double* part,
+                         const double* rz_cur, double* rz_next, double* rr_out, cudaStream_t st);
 
 // Lower-primitive stencil assembly (setup): pass 0 counts columns per row,
 // pass 1 fills the sliced ELL rows and the diagonal.

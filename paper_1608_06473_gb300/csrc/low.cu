@@ -184,50 +184,6 @@ __global__ void sum_kernel(const double* __restrict__ partial, int n, double* ou
   if (threadIdx.x == 0) out[0] = v;
 }
 
-__global__ void dot_kernel(const double* __restrict__ a, const double* __restrict__ b, int64_t n, double* partial) {
-  double v = 0.0;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-    v = fma(a[t], b[t], v);
-  v = block_sum(v);
-  if (threadIdx.x == 0) partial[blockIdx.x] = v;
-}
-
-__global__ void cg_update_kernel(double* x, double* r, double* z, const double* p, const double* q, const double* dinv,
-                                 const double* num, const double* den, int64_t n) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const double d = *den;
-  const double alpha = d != 0.0 ? *num / d : 0.0;
-  x[t] = fma(alpha, p[t], x[t]);
-  const double rr = fma(-alpha, q[t], r[t]);
-  r[t] = rr;
-  z[t] = rr * dinv[t];
-}
-
-__global__ void cg_dir_kernel(double* p, const double* z, const double* num_new, const double* num_old, int64_t n) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const double o = *num_old;
-  const double beta = o != 0.0 ? *num_new / o : 0.0;
-  p[t] = fma(beta, p[t], z[t]);
-}
-
-__global__ void coarse_diag_kernel(LevelView<double> lv, double* dinv) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= lv.n_total) return;
-  if (t < lv.off_C) {
-    const double d = lv.low_diag[t];
-    dinv[t] = d != 0.0 ? 1.0 / d : 0.0;
-  } else {
-    const int64_t q = t - lv.off_C;
-    const int c = (int)(q / lv.n_int);
-    const uint32_t p = lv.int_ijk[q % lv.n_int];
-    double s[15];
-    ifem_stencil(lv.geom[c], lv.N, unpack_i(p), unpack_j(p), unpack_k(p), s);
-    dinv[t] = 1.0 / s[MC];
-  }
-}
-
 template <class T>
 __global__ void copy_cast_kernel(const double* __restrict__ src, T* __restrict__ dst, int64_t n) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -325,11 +281,6 @@ int low_blocks(int64_t rows) {
   return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
 }
 
-int dot_blocks(int64_t n) {
-  const int64_t b = (n + 255) / 256;
-  return (int)(b < 1024 ? (b > 0 ? b : 1) : 1024);
-}
-
 template <class T>
 void launch_halo(const LevelView<T>& lv, const T* u, cudaStream_t st) {
   const int64_t n = (int64_t)lv.nC * lv.n_bnd;
@@ -386,32 +337,6 @@ void launch_restrict(const LevelView<T>& fine, const LevelView<T>& coarse, const
 
 void launch_sum(const double* partial, int n, double* out, cudaStream_t st) {
   sum_kernel<<<1, 1024, 0, st>>>(partial, n, out);
-  HHG_CUDA(cudaGetLastError());
-  count_launch();
-}
-
-void launch_dot_partial(const double* a, const double* b, int64_t n, double* partial, int nblk, cudaStream_t st) {
-  dot_kernel<<<nblk, 256, 0, st>>>(a, b, n, partial);
-  HHG_CUDA(cudaGetLastError());
-  count_launch();
-}
-
-void launch_cg_update(double* x, double* r, double* z, const double* p, const double* q, const double* dinv,
-                      const double* num, const double* den, int64_t n, cudaStream_t st) {
-  cg_update_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, r, z, p, q, dinv, num, den, n);
-  HHG_CUDA(cudaGetLastError());
-  count_launch();
-}
-
-void launch_cg_dir(double* p, const double* z, const double* num_new, const double* num_old, int64_t n,
-                   cudaStream_t st) {
-  cg_dir_kernel<<<grid_for(n, 256), 256, 0, st>>>(p, z, num_new, num_old, n);
-  HHG_CUDA(cudaGetLastError());
-  count_launch();
-}
-
-void launch_coarse_diag(const LevelView<double>& lv, double* dinv, cudaStream_t st) {
-  coarse_diag_kernel<<<grid_for(lv.n_total, 128), 128, 0, st>>>(lv, dinv);
   HHG_CUDA(cudaGetLastError());
   count_launch();
 }

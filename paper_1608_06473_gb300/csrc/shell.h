@@ -137,6 +137,7 @@ struct hhg_shell {
   double* d_red = nullptr;             // reduction scratch (partials + results)
   int64_t red_len = 0;
   double* d_cg = nullptr;              // coarse-solver vectors
+  void* coarse_op = nullptr;           // hhg::CoarseOp of the N = 4 level (owned)
   double* d_stage[3] = {nullptr, nullptr, nullptr};  // staging for host-pointer arguments
   int64_t stage_len = 0;
 
