@@ -78,6 +78,12 @@ typedef enum {
   HHG_OP_LSQP = 1      /* least-squares surrogate stencils (Sec. 3.2) */
 } hhg_op;
 
+/* Arithmetic of a call.  hhg_apply / hhg_residual / hhg_smooth: the vectors
+ * and the arithmetic are FP64 or FP32.  hhg_vcycle: f and u are always FP64
+ * vectors; HHG_F64 runs FP64 V-cycles, HHG_F32 runs mixed precision --
+ * iterative refinement with an FP64 residual (the stopping test is on it),
+ * each correction from one V-cycle whose smoothing, residuals and transfers
+ * are FP32 and whose coarsest solve is FP64.  The surrogate fit is FP64. */
 typedef enum {
   HHG_F64 = 0,
   HHG_F32 = 1

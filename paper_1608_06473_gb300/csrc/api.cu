@@ -297,7 +297,7 @@ static void build_level(hhg_shell* s, int n, cudaStream_t st) {
   HHG_CUDA(cudaMemsetAsync(L.d_ghost64, 0, sizeof(double) * lay.nC * lay.n_full, st));
   L.d_r = A.alloc_n<double>((size_t)lay.n_total);
   L.d_tmp = A.alloc_n<double>((size_t)std::max(L.max_step, 1));
-  if (n + 2 < s->Lf) {
+  if (n + 2 < s->Lf || n == 0) {
     L.d_u = A.alloc_n<double>((size_t)lay.n_total);
     L.d_f = A.alloc_n<double>((size_t)lay.n_total);
     HHG_CUDA(cudaMemsetAsync(L.d_u, 0, sizeof(double) * lay.n_total, st));
@@ -325,6 +325,55 @@ LevelView<double> view<double>(hhg_shell* s, int n) {
   v.sell_ptr = L.d_sell_ptr; v.sell_col = L.d_sell_col; v.sell_val = L.d_sell_val; v.low_diag = L.d_low_diag;
   return v;
 }
+
+// FP32 buffers of every level, allocated on the first FP32 call: halo
+// copies, work vectors and FP32 copies of the lower-primitive rows.
+static void ensure_f32(hhg_shell* s, cudaStream_t st) {
+  if (s->f32_ready) return;
+  Allocator& A = s->alloc;
+  for (auto& L : s->levels) {
+    const LevelLayout& lay = L.lay;
+    L.d_ghost32 = A.alloc_n<float>((size_t)(lay.nC * lay.n_full));
+    HHG_CUDA(cudaMemsetAsync(L.d_ghost32, 0, sizeof(float) * lay.nC * lay.n_full, st));
+    for (float** v : {&L.d_u32, &L.d_f32, &L.d_r32}) {
+      *v = A.alloc_n<float>((size_t)lay.n_total);
+      HHG_CUDA(cudaMemsetAsync(*v, 0, sizeof(float) * lay.n_total, st));
+    }
+    L.d_tmp32 = A.alloc_n<float>((size_t)std::max(L.max_step, 1));
+    int64_t nsell = 0;
+    HHG_CUDA(cudaMemcpyAsync(&nsell, L.d_sell_ptr + L.n_slices, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    HHG_CUDA(cudaStreamSynchronize(st));
+    L.d_sell_val32 = A.alloc_n<float>((size_t)std::max<int64_t>(nsell, 1));
+    L.d_low_diag32 = A.alloc_n<float>((size_t)std::max<int64_t>(lay.off_C, 1));
+    launch_copy_cast<float>(L.d_sell_val, L.d_sell_val32, nsell, st);
+    launch_copy_cast<float>(L.d_low_diag, L.d_low_diag32, lay.off_C, st);
+  }
+  HHG_CUDA(cudaStreamSynchronize(st));
+  s->f32_ready = true;
+}
+
+template <>
+LevelView<float> view<float>(hhg_shell* s, int n) {
+  const LevelView<double> d = view<double>(s, n);
+  Level& L = s->levels[n];
+  LevelView<float> v{};
+  v.N = d.N; v.nC = d.nC; v.off_E = d.off_E; v.off_F = d.off_F; v.off_C = d.off_C;
+  v.n_total = d.n_total; v.n_int = d.n_int; v.n_full = d.n_full; v.n_bnd = d.n_bnd;
+  v.geom = d.geom; v.plane_nodes = d.plane_nodes; v.plane_off = d.plane_off; v.int_ijk = d.int_ijk;
+  v.bnd_ijk = d.bnd_ijk; v.bnd_slot = d.bnd_slot; v.halo_src = d.halo_src; v.ghost = L.d_ghost32;
+  v.coef = L.d_coef32; v.q = d.q;
+  v.colour_nodes = d.colour_nodes;
+  for (int cc = 0; cc < 5; ++cc) v.colour_off[cc] = d.colour_off[cc];
+  v.sell_ptr = d.sell_ptr; v.sell_col = d.sell_col; v.sell_val = L.d_sell_val32; v.low_diag = L.d_low_diag32;
+  return v;
+}
+
+template <class T>
+static T* step_tmp(Level& L);
+template <>
+double* step_tmp<double>(Level& L) { return L.d_tmp; }
+template <>
+float* step_tmp<float>(Level& L) { return L.d_tmp32; }
 
 // ---------------------------------------------------------------------------
 // diagnostics: CUDA events around the finest-level cell kernels
@@ -372,38 +421,40 @@ static void check_op(hhg_shell* s, int n, int op) {
 
 static int eff_op(hhg_shell* s, int n, int op) { return (s->levels[n].N >= 8) ? op : HHG_OP_IFEM; }
 
-static void op_apply(hhg_shell* s, int n, int op, const double* u, double* y, cudaStream_t st) {
-  LevelView<double> v = view<double>(s, n);
+template <class T = double>
+static void op_apply(hhg_shell* s, int n, int op, const T* u, T* y, cudaStream_t st) {
+  LevelView<T> v = view<T>(s, n);
   launch_halo(v, u, st);
   {
     TimedScope ts(s, n, HHG_T_CELL_APPLY, st);
-    launch_cell(v, eff_op(s, n, op), APPLY, const_cast<double*>(u), y, (const double*)nullptr, nullptr, st);
+    launch_cell(v, eff_op(s, n, op), APPLY, const_cast<T*>(u), y, (const T*)nullptr, nullptr, st);
   }
-  launch_low(v, APPLY, u, y, (const double*)nullptr, nullptr, low_blocks(v.off_C), st);
+  launch_low(v, APPLY, u, y, (const T*)nullptr, nullptr, low_blocks(v.off_C), st);
 }
 
 // r = f - L u; the squared norm lands in d_red[slot] (device).
-static void op_residual(hhg_shell* s, int n, int op, const double* u, const double* f, double* r, int slot,
-                        cudaStream_t st) {
+template <class T = double>
+static void op_residual(hhg_shell* s, int n, int op, const T* u, const T* f, T* r, int slot, cudaStream_t st) {
   TimedScope all(s, -1, HHG_T_RESIDUAL, st);
-  LevelView<double> v = view<double>(s, n);
+  LevelView<T> v = view<T>(s, n);
   const int nb = low_blocks(v.off_C);
   double* part = s->d_red + 64;
   launch_halo(v, u, st);
   {
     TimedScope ts(s, n, HHG_T_CELL_RESIDUAL, st);
-    launch_cell(v, eff_op(s, n, op), RESIDUAL, const_cast<double*>(u), r, f, part, st);
+    launch_cell(v, eff_op(s, n, op), RESIDUAL, const_cast<T*>(u), r, f, part, st);
   }
   launch_low(v, RESIDUAL, u, r, f, part + v.nC, nb, st);
   launch_sum(part, v.nC + nb, s->d_red + slot, st);
 }
 
-static void op_smooth(hhg_shell* s, int n, int op, const double* f, double* u, cudaStream_t st) {
+template <class T = double>
+static void op_smooth(hhg_shell* s, int n, int op, const T* f, T* u, cudaStream_t st) {
   TimedScope all(s, -1, HHG_T_SMOOTH, st);
-  LevelView<double> v = view<double>(s, n);
+  LevelView<T> v = view<T>(s, n);
   Level& L = s->levels[n];
-  for (int t = 0; t < 6; ++t) launch_low_step(v, L.d_step[t], L.step_n[t], u, f, L.d_tmp, st);
-  launch_halo(v, (const double*)u, st);
+  for (int t = 0; t < 6; ++t) launch_low_step(v, L.d_step[t], L.step_n[t], u, f, step_tmp<T>(L), st);
+  launch_halo(v, (const T*)u, st);
   TimedScope ts(s, n, HHG_T_CELL_SMOOTH, st);
   launch_cell(v, eff_op(s, n, op), SMOOTH, u, u, f, nullptr, st);
 }
@@ -467,6 +518,36 @@ static void vcycle_rec(hhg_shell* s, int n, int op, const double* f, double* u, 
     launch_prolong_add(vf, vc, L.d_low_par, (const double*)C.d_u, u, st);
   }
   for (int t = 0; t < nu2; ++t) op_smooth(s, n, op, f, u, st);
+}
+
+// The inner cycle of the mixed-precision solve: the same V-cycle in FP32 on
+// levels N >= 8 (smoothing, residual, transfers), the FP64 coarse solve on
+// N = 4 (FP32 right-hand side widened, solution narrowed).
+static void vcycle_rec32(hhg_shell* s, int n, int op, const float* f, float* u, int nu1, int nu2, cudaStream_t st) {
+  if (n == 0) {
+    Level& C = s->levels[0];
+    launch_widen(f, C.d_f, C.lay.n_total, false, st);
+    coarse_solve(s, C.d_f, C.d_u, st);
+    launch_copy_cast<float>(C.d_u, u, C.lay.n_total, st);
+    return;
+  }
+  Level& L = s->levels[n];
+  Level& C = s->levels[n - 1];
+  for (int t = 0; t < nu1; ++t) op_smooth<float>(s, n, op, f, u, st);
+  op_residual<float>(s, n, op, u, f, L.d_r32, 8, st);
+  LevelView<float> vf = view<float>(s, n), vc = view<float>(s, n - 1);
+  {
+    TimedScope tr(s, -1, HHG_T_TRANSFER, st);
+    launch_restrict(vf, vc, C.d_coarse_low_fine, (const float*)L.d_r32, C.d_f32, st);
+  }
+  HHG_CUDA(cudaMemsetAsync(C.d_u32, 0, sizeof(float) * C.lay.n_total, st));
+  vcycle_rec32(s, n - 1, op, C.d_f32, C.d_u32, nu1, nu2, st);
+  {
+    TimedScope tr(s, -1, HHG_T_TRANSFER, st);
+    launch_halo(vc, (const float*)C.d_u32, st);
+    launch_prolong_add(vf, vc, L.d_low_par, (const float*)C.d_u32, u, st);
+  }
+  for (int t = 0; t < nu2; ++t) op_smooth<float>(s, n, op, f, u, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -560,13 +641,16 @@ static bool is_host_ptr(const void* p) {
 // Device view of a (possibly host) vector argument of n doubles.
 struct Arg {
   const void* user;
-  double* dev;
+  double* dev;   // device address (of doubles or floats, see elem)
   bool host;
+  size_t elem;
+  float* dev32() const { return reinterpret_cast<float*>(dev); }
 };
 
-static Arg stage_in(hhg_shell* s, int slot, const void* p, int64_t n, bool copy, cudaStream_t st) {
+static Arg stage_in(hhg_shell* s, int slot, const void* p, int64_t n, bool copy, cudaStream_t st,
+                    size_t elem = sizeof(double)) {
   HHG_CHECK(p != nullptr, HHG_EINVAL, "NULL vector argument");
-  Arg a{p, (double*)p, is_host_ptr(p)};
+  Arg a{p, (double*)p, is_host_ptr(p), elem};
   if (a.host) {
     if (s->stage_len < n) {
       for (auto& d : s->d_stage) { s->alloc.release(d); d = nullptr; }
@@ -575,14 +659,14 @@ static Arg stage_in(hhg_shell* s, int slot, const void* p, int64_t n, bool copy,
       s->stage_len = n;
     }
     a.dev = s->d_stage[slot];
-    if (copy) HHG_CUDA(cudaMemcpyAsync(a.dev, p, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    if (copy) HHG_CUDA(cudaMemcpyAsync(a.dev, p, elem * n, cudaMemcpyHostToDevice, st));
   }
   return a;
 }
 
 static void stage_out(const Arg& a, int64_t n, cudaStream_t st) {
   if (a.host) {
-    HHG_CUDA(cudaMemcpyAsync(const_cast<void*>(a.user), a.dev, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    HHG_CUDA(cudaMemcpyAsync(const_cast<void*>(a.user), a.dev, a.elem * n, cudaMemcpyDeviceToHost, st));
     HHG_CUDA(cudaStreamSynchronize(st));
   }
 }
@@ -751,7 +835,7 @@ hhg_status hhg_fit_surrogate(hhg_shell* s, int q, int j, void* stream) {
 }
 
 static void check_common(hhg_shell* s, int n, int op, int dtype, int nrhs) {
-  HHG_CHECK(dtype == HHG_F64, HHG_EINVAL, "only HHG_F64 is implemented for this entry point");
+  HHG_CHECK(dtype == HHG_F64 || dtype == HHG_F32, HHG_EINVAL, "dtype must be HHG_F64 or HHG_F32");
   HHG_CHECK(nrhs >= 1, HHG_EINVAL, "nrhs must be >= 1");
   check_op(s, n, op);
 }
@@ -764,7 +848,15 @@ hhg_status hhg_apply(hhg_shell* s, int L, hhg_op op, hhg_dtype dtype, const void
     HHG_CHECK(u != y, HHG_EINVAL, "u and y must not overlap");
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t nt = s->levels[n].lay.n_total;
+    if (dtype == HHG_F32) ensure_f32(s, st);
     for (int b = 0; b < nrhs; ++b) {
+      if (dtype == HHG_F32) {
+        Arg au = stage_in(s, 0, (const float*)u + b * nt, nt, true, st, sizeof(float));
+        Arg ay = stage_in(s, 1, (float*)y + b * nt, nt, false, st, sizeof(float));
+        op_apply<float>(s, n, op, au.dev32(), ay.dev32(), st);
+        stage_out(ay, nt, st);
+        continue;
+      }
       Arg au = stage_in(s, 0, (const double*)u + b * nt, nt, true, st);
       Arg ay = stage_in(s, 1, (double*)y + b * nt, nt, false, st);
       op_apply(s, n, op, au.dev, ay.dev, st);
@@ -780,12 +872,21 @@ hhg_status hhg_residual(hhg_shell* s, int L, hhg_op op, hhg_dtype dtype, const v
     check_common(s, n, op, dtype, nrhs);
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t nt = s->levels[n].lay.n_total;
+    if (dtype == HHG_F32) ensure_f32(s, st);
     for (int b = 0; b < nrhs; ++b) {
-      Arg au = stage_in(s, 0, (const double*)u + b * nt, nt, true, st);
-      Arg af = stage_in(s, 1, (const double*)f + b * nt, nt, true, st);
-      Arg ar = stage_in(s, 2, (double*)r + b * nt, nt, false, st);
-      op_residual(s, n, op, au.dev, af.dev, ar.dev, 9, st);
-      stage_out(ar, nt, st);
+      if (dtype == HHG_F32) {
+        Arg au = stage_in(s, 0, (const float*)u + b * nt, nt, true, st, sizeof(float));
+        Arg af = stage_in(s, 1, (const float*)f + b * nt, nt, true, st, sizeof(float));
+        Arg ar = stage_in(s, 2, (float*)r + b * nt, nt, false, st, sizeof(float));
+        op_residual<float>(s, n, op, au.dev32(), af.dev32(), ar.dev32(), 9, st);
+        stage_out(ar, nt, st);
+      } else {
+        Arg au = stage_in(s, 0, (const double*)u + b * nt, nt, true, st);
+        Arg af = stage_in(s, 1, (const double*)f + b * nt, nt, true, st);
+        Arg ar = stage_in(s, 2, (double*)r + b * nt, nt, false, st);
+        op_residual(s, n, op, au.dev, af.dev, ar.dev, 9, st);
+        stage_out(ar, nt, st);
+      }
       if (norms) norms[b] = std::sqrt(read_scalar(s, 9, st));
     }
   });
@@ -800,7 +901,16 @@ hhg_status hhg_smooth(hhg_shell* s, int L, hhg_op op, hhg_dtype dtype, const voi
     cudaStream_t st = (cudaStream_t)stream;
     Level& Lv = s->levels[n];
     const int64_t nt = Lv.lay.n_total;
+    if (dtype == HHG_F32) ensure_f32(s, st);
     for (int b = 0; b < nrhs; ++b) {
+      if (dtype == HHG_F32) {
+        Arg af = stage_in(s, 1, (const float*)f + b * nt, nt, true, st, sizeof(float));
+        Arg au = stage_in(s, 0, (float*)u + b * nt, nt, true, st, sizeof(float));
+        launch_zero_list(Lv.d_dirichlet, Lv.n_dirichlet, au.dev32(), st);
+        for (int t = 0; t < sweeps; ++t) op_smooth<float>(s, n, op, af.dev32(), au.dev32(), st);
+        stage_out(au, nt, st);
+        continue;
+      }
       Arg af = stage_in(s, 1, (const double*)f + b * nt, nt, true, st);
       Arg au = stage_in(s, 0, (double*)u + b * nt, nt, true, st);
       launch_zero_list(Lv.d_dirichlet, Lv.n_dirichlet, au.dev, st);
@@ -832,8 +942,17 @@ hhg_status hhg_vcycle(hhg_shell* s, hhg_op op, hhg_dtype dtype, const void* f, v
       HHG_CHECK(std::isfinite(r0), HHG_EDIVERGED, "initial residual is not finite");
       double rel = r0 > 0 ? 1.0 : 0.0;
       int cyc = 0;
+      if (dtype == HHG_F32) ensure_f32(s, st);
       while (rel > rtol && cyc < max_cycles) {
-        vcycle_rec(s, n, op, af.dev, au.dev, nu1, nu2, st);
+        if (dtype == HHG_F32) {
+          // iterative refinement: e = one FP32 V-cycle on L e = r (e0 = 0), u += e
+          launch_copy_cast<float>(Lv.d_r, Lv.d_f32, nt, st);
+          HHG_CUDA(cudaMemsetAsync(Lv.d_u32, 0, sizeof(float) * nt, st));
+          vcycle_rec32(s, n, op, Lv.d_f32, Lv.d_u32, nu1, nu2, st);
+          launch_widen(Lv.d_u32, au.dev, nt, true, st);
+        } else {
+          vcycle_rec(s, n, op, af.dev, au.dev, nu1, nu2, st);
+        }
         op_residual(s, n, op, au.dev, af.dev, Lv.d_r, 10, st);
         const double rn = std::sqrt(read_scalar(s, 10, st));
         HHG_CHECK(std::isfinite(rn), HHG_EDIVERGED, "residual norm became NaN or Inf");

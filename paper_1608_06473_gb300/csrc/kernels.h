@@ -72,6 +72,8 @@ void launch_sum(const double* partial, int n, double* out, cudaStream_t st);
 
 template <class T>
 void launch_copy_cast(const double* src, T* dst, int64_t n, cudaStream_t st);
+// dst = (double) src, or dst += (double) src when add
+void launch_widen(const float* src, double* dst, int64_t n, bool add, cudaStream_t st);
 
 // ---- coarsest-level conjugate gradients (coarse.cu) -------------------------
 constexpr int CG_BLOCKS = 128;

@@ -190,6 +190,11 @@ __global__ void copy_cast_kernel(const double* __restrict__ src, T* __restrict__
   if (t < n) dst[t] = (T)src[t];
 }
 
+__global__ void widen_kernel(const float* __restrict__ src, double* __restrict__ dst, int64_t n, int add) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) dst[t] = add ? dst[t] + (double)src[t] : (double)src[t];
+}
+
 // Canonical index of the neighbour of a cell's boundary point, or -1 when it
 // is a Dirichlet point (dropped from the rows: Dirichlet values are 0).
 __device__ __forceinline__ int64_t nb_index(const LevelView<double>& lv, int c, int i, int j, int k) {
@@ -345,6 +350,13 @@ template <class T>
 void launch_copy_cast(const double* src, T* dst, int64_t n, cudaStream_t st) {
   if (n == 0) return;
   copy_cast_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(src, dst, n);
+  HHG_CUDA(cudaGetLastError());
+  count_launch();
+}
+
+void launch_widen(const float* src, double* dst, int64_t n, bool add, cudaStream_t st) {
+  if (n == 0) return;
+  widen_kernel<<<grid_for(n, 256), 256, 0, st>>>(src, dst, n, add ? 1 : 0);
   HHG_CUDA(cudaGetLastError());
   count_launch();
 }

@@ -112,6 +112,11 @@ struct Level {
   double* d_f = nullptr;
   double* d_r = nullptr;
   double* d_tmp = nullptr;  // step buffer for simultaneous lower-primitive updates
+  // FP32 work vectors of the mixed-precision cycle (allocated on first use)
+  float* d_u32 = nullptr;
+  float* d_f32 = nullptr;
+  float* d_r32 = nullptr;
+  float* d_tmp32 = nullptr;
 };
 
 // Number of monomials of total degree <= q in three variables (Eq. 3.2).
@@ -139,6 +144,7 @@ struct hhg_shell {
   double* d_cg = nullptr;              // coarse-solver vectors
   void* coarse_op = nullptr;           // hhg::CoarseOp of the N = 4 level (owned)
   double* d_stage[3] = {nullptr, nullptr, nullptr};  // staging for host-pointer arguments
+  bool f32_ready = false;              // FP32 resources allocated
   int64_t stage_len = 0;
 
   // diagnostics: CUDA-event pairs around timed kernel launches
