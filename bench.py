@@ -42,10 +42,13 @@ WORKLOADS = {
     # name: (tang, layers, L, description)
     "shell3840_N64": (2, 4, 6, "3840 macro cells (icosahedral shell, 2 surface refinements, 4 layers), "
                                "N=64 intervals per macro edge, r in [0.55, 1]"),
+    "shell3840_N128": (2, 4, 7, "3840 macro cells (icosahedral shell, 2 surface refinements, 4 layers), "
+                                 "N=128 intervals per macro edge, r in [0.55, 1]"),
     "shell480_N64": (1, 2, 6, "480 macro cells (icosahedral shell, 1 surface refinement, 2 layers), N=64, "
                               "r in [0.55, 1]"),
     "shell60_N16": (0, 1, 4, "60 macro cells (icosahedral shell, 1 layer), N=16, r in [0.55, 1]"),
 }
+HBM_MEASURED_GBS = 6794.8    # MEASURED_PEAKS.json: copy bandwidth on the GB300s
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (recipe's nominal figure: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)
 LSQP_FLOPS = {1: 44, 2: 59, 3: 74}   # Table 4.2: 29 + 15 q flops per stencil-based update
 
@@ -65,6 +68,10 @@ def parse():
                    help="solve: the whole path per step (default); smoother: finest-level sweeps only "
                         "(for profiling the smoother kernels)")
     p.add_argument("--op", choices=["lsqp", "ifem"], default="lsqp", help="operator for --mode smoother")
+    p.add_argument("--precision", choices=["f64", "mixed"], default="f64",
+                   help="f64: FP64 V-cycles; mixed: FP32 V-cycles inside FP64 iterative refinement")
+    p.add_argument("--compare-f64", action="store_true",
+                   help="with --precision mixed: also time one plain FP64 solve and report the speedup")
     return p.parse_args()
 
 
@@ -183,13 +190,14 @@ def run_ours(args, rank, world, local):
     f = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_F)).cuda()
     u = torch.zeros(n_total, dtype=torch.float64, device="cuda")
     op = hhg.HHG_OP_LSQP
+    dtype = hhg.HHG_F32 if args.precision == "mixed" else hhg.HHG_F64
     nu1 = nu2 = 3
 
     def step(fv, uv):
         s.fit(args.q, args.j, stream=stream)
         if isinstance(uv, torch.Tensor) and uv.is_cuda:
             uv.zero_()
-        rel, cycles, _ = s.vcycle(fv, uv, nu1, nu2, max_cycles=60, rtol=1e-8, op=op, stream=stream)
+        rel, cycles, _ = s.vcycle(fv, uv, nu1, nu2, max_cycles=60, rtol=1e-8, op=op, dtype=dtype, stream=stream)
         return rel[0], cycles
 
     def updates(cycles):
@@ -231,19 +239,32 @@ def run_ours(args, rank, world, local):
     hhg.hhg_timing(s.handle, False)
 
     # smoother alone: one sweep of the finest level (all 10 steps)
+    sdt = torch.float32 if args.precision == "mixed" else torch.float64
+
     def sweep_glups(opcode, reps):
-        uu = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_U)).cuda()
-        s.smooth(f, uu, 1, op=opcode, stream=stream)
+        uu = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_U)).cuda().to(sdt)
+        ff = f.to(sdt)
+        s.smooth(ff, uu, 1, op=opcode, dtype=dtype, stream=stream)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        s.smooth(f, uu, reps, op=opcode, stream=stream)
+        s.smooth(ff, uu, reps, op=opcode, dtype=dtype, stream=stream)
         b.record(stream)
         torch.cuda.synchronize()
         return n_free * reps / (a.elapsed_time(b) * 1e-3) / 1e9
 
     g_lsqp = sweep_glups(hhg.HHG_OP_LSQP, 3)
     g_ifem = sweep_glups(hhg.HHG_OP_IFEM, 1)
+    f64_solve = None
+    if args.precision == "mixed" and args.compare_f64:
+        u.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rel64, cyc64, _ = s.vcycle(f, u, nu1, nu2, max_cycles=60, rtol=1e-8, op=op, dtype=hhg.HHG_F64, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        f64_solve = {"s": a.elapsed_time(b) * 1e-3, "cycles": cyc64, "relres": float(rel64[0])}
 
     # end to end through host buffers (pinned): H2D of f and u, D2H of u per step
     e2e = None
@@ -269,22 +290,30 @@ def run_ours(args, rank, world, local):
     units_per_launch = n_cells * (N - 1) * (N - 2) * (N - 3) // 6
     avg_launch_s = sm_ms * 1e-3 / max(sm_n, 1)
     flops = LSQP_FLOPS[args.q] * units_per_launch
-    achieved = flops / avg_launch_s / 1e12
-    traffic = traffic_record("lsqp_cell_smooth_f64", args.workload)
-    roofline = {"kernel": "lsqp_node_kernel<%d,SMOOTH> (finest level; one sweep = 4 colour launches)" % args.q,
-                "bound": "alu",
-                "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": traffic,
-                "launches": sm_n, "avg_launch_ms": avg_launch_s * 1e3,
-                "algorithmic_flops_per_launch": flops,
-                "algorithmic_bytes_per_launch": 24 * units_per_launch,
-                "achieved_hbm_gbs_algorithmic": 24 * units_per_launch / avg_launch_s / 1e9,
-                "peak_note": "FP64 nominal (recipe); HBM measured copy 6794.8 GB/s"}
+    if args.precision == "f64":
+        achieved = flops / avg_launch_s / 1e12
+        roofline = {"kernel": "lsqp_node_kernel<%d,SMOOTH> (finest level; one sweep = 4 colour launches)" % args.q,
+                    "bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_NOMINAL_TFLOPS,
+                    "traffic": traffic_record("lsqp_node_smooth_f64", args.workload),
+                    "peak_note": "FP64 nominal (recipe: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz)"}
+    else:
+        achieved = 12 * units_per_launch / avg_launch_s / 1e9
+        roofline = {"kernel": "lsqp_wave_kernel<float,%d,SMOOTH> (finest level, one launch per sweep)" % args.q,
+                    "bound": "hbm", "achieved": achieved, "peak": HBM_MEASURED_GBS, "unit": "GB/s",
+                    "frac": achieved / HBM_MEASURED_GBS,
+                    "traffic": traffic_record("lsqp_wave_smooth_f32", args.workload),
+                    "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)"}
+    roofline.update({"launches": sm_n, "avg_launch_ms": avg_launch_s * 1e3,
+                     "algorithmic_flops_per_launch": flops,
+                     "algorithmic_bytes_per_launch": (24 if args.precision == "f64" else 12) * units_per_launch})
     value = tot_updates * world / (ms * 1e-3) / 1e9
     out = {"metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "vs_baseline": None, "dtype": "f64" if args.precision == "f64" else "f32 (inner cycles) + f64 (refinement)",
+           "data": "synthetic",
            "config": {"workload": args.workload, "shell": desc, "op": "lsqp", "q": args.q, "j": args.j,
+                      "precision": args.precision,
                       "cycle": "V(3,3)", "rtol": 1e-8, "unknowns": n_free, "nodes": n_total,
                       "l2": "inputs larger than L2 (each FP64 vector %.2f GB)" % (8 * n_total / 1e9),
                       "parallelism": "replicas" if world > 1 else "single"},
@@ -292,7 +321,8 @@ def run_ours(args, rank, world, local):
            "e2e": e2e,
            "smoother_glups": {"lsqp": g_lsqp, "ifem": g_ifem, "lsqp_over_ifem": g_lsqp / g_ifem},
            "vcycle_s_to_1e-8": ms * 1e-3 / args.steps, "cycles": cyc_list, "final_relres": max(rels),
-           "breakdown": breakdown}
+           "breakdown": breakdown, "f64_solve": f64_solve,
+           "speedup_over_f64_solve": (f64_solve["s"] / (ms * 1e-3 / args.steps)) if f64_solve else None}
     s.close()
     return out
 
@@ -371,18 +401,21 @@ def run_smoother(args):
     opcode = hhg.HHG_OP_LSQP if args.op == "lsqp" else hhg.HHG_OP_IFEM
     if opcode == hhg.HHG_OP_LSQP:
         s.fit(args.q, args.j, stream=stream)
-    f = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_F)).cuda()
-    u = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_U)).cuda()
-    s.smooth(f, u, args.warmup, op=opcode, stream=stream)
+    dt = torch.float32 if args.precision == "mixed" else torch.float64
+    dtype = hhg.HHG_F32 if args.precision == "mixed" else hhg.HHG_F64
+    f = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_F)).cuda().to(dt)
+    u = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_U)).cuda().to(dt)
+    s.smooth(f, u, args.warmup, op=opcode, dtype=dtype, stream=stream)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    s.smooth(f, u, args.steps, op=opcode, stream=stream)
+    s.smooth(f, u, args.steps, op=opcode, dtype=dtype, stream=stream)
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
     s.close()
-    return {"mode": "smoother", "op": args.op, "workload": args.workload, "sweeps": args.steps,
+    return {"mode": "smoother", "op": args.op, "precision": "f32" if args.precision == "mixed" else "f64",
+            "workload": args.workload, "sweeps": args.steps,
             "ms_per_sweep": ms / args.steps, "GLUP/s": n_free * args.steps / (ms * 1e-3) / 1e9}
 
 

@@ -133,27 +133,40 @@ static void build_level(hhg_shell* s, int n, cudaStream_t st) {
   // cell-local tables shared by all cells
   std::vector<uint32_t> plane_nodes;
   std::vector<int> plane_off(4 * (N + 1) + 1, 0);
+  // every node list puts the deep-interior points (all 14 neighbours
+  // interior) first, so warps take one addressing path
+  auto deep = [N](int i, int j, int k) { return i >= 2 && j >= 2 && k >= 2 && i + j + k <= N - 2; };
   for (int k = 0; k <= N; ++k)
     for (int cc = 0; cc < 4; ++cc) {
       plane_off[k * 4 + cc] = (int)plane_nodes.size();
-      for (int j = 1; j <= N - 2 - k; ++j)
-        for (int i = 1; i <= N - 1 - j - k; ++i)
-          if (k >= 1 && (i + 2 * j + 3 * k) % 4 == cc) plane_nodes.push_back(pack_ijk(i, j, k));
+      for (int pass = 0; pass < 2; ++pass)
+        for (int j = 1; j <= N - 2 - k; ++j)
+          for (int i = 1; i <= N - 1 - j - k; ++i)
+            if (k >= 1 && (i + 2 * j + 3 * k) % 4 == cc && deep(i, j, k) == (pass == 0))
+              plane_nodes.push_back(pack_ijk(i, j, k));
     }
   plane_off[4 * (N + 1)] = (int)plane_nodes.size();
   std::vector<uint32_t> int_ijk;
   for (int k = 1; k < N; ++k)
     for (int j = 1; j < N - k; ++j)
       for (int i = 1; i < N - j - k; ++i) int_ijk.push_back(pack_ijk(i, j, k));
-  std::vector<uint32_t> colour_nodes;
+  // colour_nodes: per colour, deep points first; all_nodes: every interior
+  // point, deep first (the apply / residual order)
+  std::vector<uint32_t> colour_nodes, all_nodes;
   for (int cc = 0; cc < 4; ++cc) {
     L.colour_off[cc] = (int)colour_nodes.size();
+    for (int pass = 0; pass < 2; ++pass)
+      for (int k = 1; k < N; ++k)
+        for (int j = 1; j < N - k; ++j)
+          for (int i = 1; i < N - j - k; ++i)
+            if ((i + 2 * j + 3 * k) % 4 == cc && deep(i, j, k) == (pass == 0)) colour_nodes.push_back(pack_ijk(i, j, k));
+  }
+  L.colour_off[4] = (int)colour_nodes.size();
+  for (int pass = 0; pass < 2; ++pass)
     for (int k = 1; k < N; ++k)
       for (int j = 1; j < N - k; ++j)
         for (int i = 1; i < N - j - k; ++i)
-          if ((i + 2 * j + 3 * k) % 4 == cc) colour_nodes.push_back(pack_ijk(i, j, k));
-  }
-  L.colour_off[4] = (int)colour_nodes.size();
+          if (deep(i, j, k) == (pass == 0)) all_nodes.push_back(pack_ijk(i, j, k));
   std::vector<uint32_t> bnd_ijk;
   std::vector<int> bnd_slot((size_t)lay.n_full, -1);
   for (int k = 0; k <= N; ++k)
@@ -214,6 +227,7 @@ static void build_level(hhg_shell* s, int n, cudaStream_t st) {
   L.d_plane_off = upload(A, plane_off, st);
   L.d_int_ijk = upload(A, int_ijk, st);
   L.d_colour_nodes = upload(A, colour_nodes, st);
+  L.d_all_nodes = upload(A, all_nodes, st);
   L.d_bnd_ijk = upload(A, bnd_ijk, st);
   L.d_bnd_slot = upload(A, bnd_slot, st);
   L.d_halo_src = upload(A, halo_src, st);
@@ -321,6 +335,7 @@ LevelView<double> view<double>(hhg_shell* s, int n) {
   v.coef = L.d_coef; v.q = (L.d_coef && L.N >= 8) ? s->q : 0;
   v.line64 = L.d_line64; v.cell_e = L.d_cell_e; v.n_lines = (int)n_cell_lines(L.N);
   v.colour_nodes = L.d_colour_nodes;
+  v.all_nodes = L.d_all_nodes;
   for (int cc = 0; cc < 5; ++cc) v.colour_off[cc] = L.colour_off[cc];
   v.sell_ptr = L.d_sell_ptr; v.sell_col = L.d_sell_col; v.sell_val = L.d_sell_val; v.low_diag = L.d_low_diag;
   return v;
@@ -363,6 +378,7 @@ LevelView<float> view<float>(hhg_shell* s, int n) {
   v.bnd_ijk = d.bnd_ijk; v.bnd_slot = d.bnd_slot; v.halo_src = d.halo_src; v.ghost = L.d_ghost32;
   v.coef = L.d_coef32; v.q = d.q;
   v.colour_nodes = d.colour_nodes;
+  v.all_nodes = d.all_nodes;
   for (int cc = 0; cc < 5; ++cc) v.colour_off[cc] = d.colour_off[cc];
   v.sell_ptr = d.sell_ptr; v.sell_col = d.sell_col; v.sell_val = L.d_sell_val32; v.low_diag = L.d_low_diag32;
   return v;

@@ -14,9 +14,10 @@
 //    once per weight; the FP64 pipe then only carries the conversions, the 14
 //    stencil products and the divide.  Kernels are thread-per-node with one
 //    CTA per macro cell and no barriers; the smoother is one launch per colour.
-//  * FP32: one CTA per cell walks its planes; the line coefficients of a plane
-//    are computed in shared memory (FP32 arithmetic is cheap, HBM traffic is
-//    the bound), and the four colours run in one launch as a plane wavefront:
+//  * FP32: one CTA per cell walks its planes; per plane k each direction's
+//    polynomial is reduced to a polynomial in (i, j) in shared memory and
+//    evaluated per node (FP32 arithmetic is cheap, HBM traffic is the
+//    bound), and the four colours run in one launch as a plane wavefront:
 //    in step s colour c is updated on plane s + 1 - c, c = 0..3, with a
 //    barrier after each colour, so every update sees all lower-colour updates
 //    of planes k - 1, k, k + 1 and none of the higher ones -- exactly four
@@ -24,6 +25,11 @@
 //
 // IFEM (Sec. 4.2.1): every node assembles its 15 weights from the 24 element
 // matrices around it (thread per node, one launch per colour).
+//
+// Neighbour addressing: nodes whose 14 neighbours are all interior use
+// closed-form 32-bit offsets within the cell's block of the canonical
+// vector; nodes next to the cell boundary read boundary neighbours from the
+// cell's halo copy.
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -33,7 +39,7 @@ namespace hhg {
 
 namespace {
 
-constexpr int WAVE_THREADS = 128;  // FP32 wavefront kernel
+constexpr int WAVE_THREADS = 256;  // FP32 wavefront kernel
 constexpr int NODE_THREADS = 256;  // thread-per-node kernels
 
 // Coefficients of the polynomial in i along line (j, k): c_a(j, k) =
@@ -69,36 +75,49 @@ __device__ __forceinline__ T eval_line(const T* cl, T i) {
   return v;
 }
 
-// Stencil application at one interior node from its 15 weights (sw may be
-// scaled by 2^E; `scale` = 2^E, `inv_scale` = 2^-E, 1 when unscaled).
-template <class T, Mode MODE>
-__device__ __forceinline__ void node_update(const LevelView<T>& lv, int c, int i, int j, int k, const T* sw,
-                                            T* u, T* out, const T* f, double& nrm, T scale, T inv_scale) {
-  const int64_t I = lv.off_C + (int64_t)c * lv.n_int + lin_interior(i, j, k, lv.N);
-  const T* uc = u;
-  if (MODE == SMOOTH) {
-    T a0 = f[I] * scale, a1 = 0;
+// Stencil application at one interior node.  wt(w) returns weight w (the
+// centre is w = MC), possibly scaled by 2^E; `scale` = 2^E, `inv_scale` =
+// 2^-E (1 when unscaled).  Deep-interior nodes read their neighbours through
+// closed-form offsets, the others through the interior / halo lookup.
+template <class T, Mode MODE, class WT>
+__device__ __forceinline__ void node_update(const LevelView<T>& lv, int c, int i, int j, int k, WT wt, T* u, T* out,
+                                            const T* f, double& nrm, T scale, T inv_scale) {
+  const int64_t base = lv.off_C + (int64_t)c * lv.n_int;
+  const int lin = lin_interior32(i, j, k, lv.N);
+  const int64_t I = base + lin;
+  auto body = [&](auto nb) {
+    if (MODE == SMOOTH) {
+      T a0 = f[I] * scale, a1 = 0;
 #pragma unroll
-    for (int w = 0; w < 14; w += 2) {
-      a0 = fma(-sw[w], load_pt(lv, uc, c, i + DI(w), j + DJ(w), k + DK(w)), a0);
-      a1 = fma(-sw[w + 1], load_pt(lv, uc, c, i + DI(w + 1), j + DJ(w + 1), k + DK(w + 1)), a1);
-    }
-    u[I] = (a0 + a1) / sw[MC];
-  } else {
-    T a0 = sw[MC] * u[I], a1 = 0;
-#pragma unroll
-    for (int w = 0; w < 14; w += 2) {
-      a0 = fma(sw[w], load_pt(lv, uc, c, i + DI(w), j + DJ(w), k + DK(w)), a0);
-      a1 = fma(sw[w + 1], load_pt(lv, uc, c, i + DI(w + 1), j + DJ(w + 1), k + DK(w + 1)), a1);
-    }
-    const T y = a0 + a1;
-    if (MODE == APPLY) {
-      out[I] = y * inv_scale;
+      for (int w = 0; w < 14; w += 2) {
+        a0 = fma(-wt(w), nb(w), a0);
+        a1 = fma(-wt(w + 1), nb(w + 1), a1);
+      }
+      u[I] = (a0 + a1) / wt(MC);
     } else {
-      const T r = fma(-inv_scale, y, f[I]);
-      out[I] = r;
-      nrm += (double)r * (double)r;
+      T a0 = wt(MC) * u[I], a1 = 0;
+#pragma unroll
+      for (int w = 0; w < 14; w += 2) {
+        a0 = fma(wt(w), nb(w), a0);
+        a1 = fma(wt(w + 1), nb(w + 1), a1);
+      }
+      const T y = a0 + a1;
+      if (MODE == APPLY) {
+        out[I] = y * inv_scale;
+      } else {
+        const T r = fma(-inv_scale, y, f[I]);
+        out[I] = r;
+        nrm += (double)r * (double)r;
+      }
     }
+  };
+  if (deep_interior(i, j, k, lv.N)) {
+    int off[14];
+    neighbour_offsets(j, k, lv.N, off);
+    const T* p = u + I;
+    body([&](int w) -> T { return p[off[w]]; });
+  } else {
+    body([&](int w) -> T { return load_pt(lv, (const T*)u, c, i + DI(w), j + DJ(w), k + DK(w)); });
   }
 }
 
@@ -153,7 +172,7 @@ __global__ void lsqp_line_table_kernel(const double* __restrict__ coef, const in
 }
 
 template <int Q, Mode MODE>
-__global__ void __launch_bounds__(NODE_THREADS) lsqp_node_kernel(LevelView<double> lv, const uint32_t* __restrict__ list,
+__global__ void __launch_bounds__(NODE_THREADS, 3) lsqp_node_kernel(LevelView<double> lv, const uint32_t* __restrict__ list,
                                                                   int n_list, double* u, double* out, const double* f,
                                                                   double* partial) {
   const int c = blockIdx.x;
@@ -166,15 +185,13 @@ __global__ void __launch_bounds__(NODE_THREADS) lsqp_node_kernel(LevelView<doubl
     const uint32_t p = list[t];
     const int i = unpack_i(p), j = unpack_j(p), k = unpack_k(p);
     const long long* C = tab + (int64_t)line_id(j, k, N) * line_rec(Q);
-    double sw[15];
-#pragma unroll
-    for (int w = 0; w < 15; ++w) {
+    auto wt = [&](int w) -> double {
       long long v = C[w * (Q + 1) + Q];
 #pragma unroll
       for (int a = Q - 1; a >= 0; --a) v = v * (long long)i + C[w * (Q + 1) + a];
-      sw[w] = (double)v;
-    }
-    node_update<double, MODE>(lv, c, i, j, k, sw, u, out, f, nrm, scale, inv_scale);
+      return (double)v;
+    };
+    node_update<double, MODE>(lv, c, i, j, k, wt, u, out, f, nrm, scale, inv_scale);
   }
   if (MODE == RESIDUAL) {
     const double tot = block_sum(nrm);
@@ -183,42 +200,80 @@ __global__ void __launch_bounds__(NODE_THREADS) lsqp_node_kernel(LevelView<doubl
 }
 
 // ---------------------------------------------------------------------------
-// FP32 surrogate: plane wavefront with shared-memory line coefficients
+// FP32 surrogate: plane wavefront, per-plane polynomials in (i, j)
 // ---------------------------------------------------------------------------
 
+// Index of A_{a,b,d} (coefficient of i^a j^b k^d) in the storage order
+// for a = 0..Q, for d = 0..Q-a, for b = 0..Q-a-d.
+template <int Q>
+__host__ __device__ constexpr int coef_index(int a, int b, int d) {
+  int t = 0;
+  for (int aa = 0; aa < a; ++aa) t += (Q - aa + 1) * (Q - aa + 2) / 2;
+  for (int dd = 0; dd < d; ++dd) t += Q - a - dd + 1;
+  return t + b;
+}
+// Per plane and direction: D_{a,b}(k) = sum_d A_{a,b,d} k^d, stored for
+// a = 0..Q, b = 0..Q-a; (Q+1)(Q+2)/2 values.
+template <int Q>
+__host__ __device__ constexpr int plane_index(int a, int b) {
+  int t = 0;
+  for (int aa = 0; aa < a; ++aa) t += Q - aa + 1;
+  return t + b;
+}
+
+template <class T, int Q>
+__device__ __forceinline__ void plane_coeffs(const T* A, T k, T* P) {
+#pragma unroll
+  for (int a = 0; a <= Q; ++a)
+#pragma unroll
+    for (int b = 0; b <= Q - a; ++b) {
+      T v = A[coef_index<Q>(a, b, Q - a - b)];
+#pragma unroll
+      for (int d = Q - a - b - 1; d >= 0; --d) v = fma(v, k, A[coef_index<Q>(a, b, d)]);
+      P[plane_index<Q>(a, b)] = v;
+    }
+}
+
+template <class T, int Q>
+__device__ __forceinline__ T eval_plane(const T* P, T i, T j) {
+  T s = 0;
+#pragma unroll
+  for (int a = Q; a >= 0; --a) {
+    T c = P[plane_index<Q>(a, Q - a)];
+#pragma unroll
+    for (int b = Q - a - 1; b >= 0; --b) c = fma(c, j, P[plane_index<Q>(a, b)]);
+    s = (a == Q) ? c : fma(s, i, c);
+  }
+  return s;
+}
+
 template <class T, int Q, Mode MODE>
-__global__ void __launch_bounds__(WAVE_THREADS) lsqp_wave_kernel(LevelView<T> lv, T* u, T* out, const T* f,
+__global__ void __launch_bounds__(WAVE_THREADS, 2) lsqp_wave_kernel(LevelView<T> lv, T* u, T* out, const T* f,
                                                                  double* partial) {
   constexpr int MQ = (Q + 1) * (Q + 2) * (Q + 3) / 6;
+  constexpr int NP = (Q + 1) * (Q + 2) / 2;       // per-plane values per direction
   constexpr int NSLOT = (MODE == SMOOTH) ? 4 : 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sA = reinterpret_cast<T*>(smem_raw);   // [15][MQ]
-  T* ring = sA + 15 * MQ;                   // [NSLOT][NL][15][Q+1]
+  __shared__ T sA[15 * MQ];
+  __shared__ T ring[NSLOT][15 * NP];
   const int c = blockIdx.x;
   const int N = lv.N;
-  const int NL = N - 3;
   for (int t = threadIdx.x; t < 15 * MQ; t += blockDim.x) sA[t] = lv.coef[(int64_t)c * 15 * MQ + t];
   __syncthreads();
   double nrm = 0.0;
 
   auto prologue = [&](int k) {
     const int slot = (NSLOT == 4) ? (k & 3) : 0;
-    for (int jj = threadIdx.x; jj < N - 2 - k; jj += blockDim.x) {
-      T* dst = ring + ((slot * NL + jj) * 15) * (Q + 1);
-#pragma unroll 1
-      for (int w = 0; w < 15; ++w) line_coeffs<T, Q>(sA + w * MQ, (T)(jj + 1), (T)k, dst + w * (Q + 1));
-    }
+    if (threadIdx.x < 15) plane_coeffs<T, Q>(sA + threadIdx.x * MQ, (T)k, &ring[slot][threadIdx.x * NP]);
   };
   auto process = [&](int k, int beg, int end) {
     const int slot = (NSLOT == 4) ? (k & 3) : 0;
     for (int t = beg + threadIdx.x; t < end; t += blockDim.x) {
       const uint32_t p = lv.plane_nodes[t];
       const int i = unpack_i(p), j = unpack_j(p);
-      const T* cl = ring + ((slot * NL + (j - 1)) * 15) * (Q + 1);
-      T sw[15];
-#pragma unroll
-      for (int w = 0; w < 15; ++w) sw[w] = eval_line<T, Q>(cl + w * (Q + 1), (T)i);
-      node_update<T, MODE>(lv, c, i, j, k, sw, u, out, f, nrm, T(1), T(1));
+      const T* P = ring[slot];
+      const T ti = (T)i, tj = (T)j;
+      auto wt = [&](int w) -> T { return eval_plane<T, Q>(P + w * NP, ti, tj); };
+      node_update<T, MODE>(lv, c, i, j, k, wt, u, out, f, nrm, T(1), T(1));
     }
   };
 
@@ -266,10 +321,8 @@ __global__ void __launch_bounds__(NODE_THREADS) ifem_node_kernel(LevelView<T> lv
     const int i = unpack_i(p), j = unpack_j(p), k = unpack_k(p);
     double s[15];
     ifem_stencil(g, lv.N, i, j, k, s);
-    T sw[15];
-#pragma unroll
-    for (int w = 0; w < 15; ++w) sw[w] = (T)s[w];
-    node_update<T, MODE>(lv, c, i, j, k, sw, u, out, f, nrm, T(1), T(1));
+    auto wt = [&](int w) -> T { return (T)s[w]; };
+    node_update<T, MODE>(lv, c, i, j, k, wt, u, out, f, nrm, T(1), T(1));
   }
   if (MODE == RESIDUAL) {
     const double tot = block_sum(nrm);
@@ -283,12 +336,7 @@ __global__ void __launch_bounds__(NODE_THREADS) ifem_node_kernel(LevelView<T> lv
 
 template <class T, int Q, Mode MODE>
 void launch_wave(const LevelView<T>& lv, T* u, T* out, const T* f, double* partial, cudaStream_t st) {
-  constexpr int MQ = (Q + 1) * (Q + 2) * (Q + 3) / 6;
-  constexpr int NSLOT = (MODE == SMOOTH) ? 4 : 1;
-  const size_t smem = sizeof(T) * (15 * MQ + (size_t)NSLOT * (lv.N - 3) * 15 * (Q + 1));
-  auto kern = lsqp_wave_kernel<T, Q, MODE>;
-  if (smem > 48 * 1024) HHG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<lv.nC, WAVE_THREADS, smem, st>>>(lv, u, out, f, partial);
+  lsqp_wave_kernel<T, Q, MODE><<<lv.nC, WAVE_THREADS, 0, st>>>(lv, u, out, f, partial);
   HHG_CUDA(cudaGetLastError());
   count_launch();
 }
@@ -306,8 +354,8 @@ template <int Q>
 void lsqp64(const LevelView<double>& lv, Mode mode, double* u, double* out, const double* f, double* partial,
             cudaStream_t st) {
   switch (mode) {
-    case APPLY: launch_node64<Q, APPLY>(lv, lv.int_ijk, (int)lv.n_int, u, out, f, partial, st); break;
-    case RESIDUAL: launch_node64<Q, RESIDUAL>(lv, lv.int_ijk, (int)lv.n_int, u, out, f, partial, st); break;
+    case APPLY: launch_node64<Q, APPLY>(lv, lv.all_nodes, (int)lv.n_int, u, out, f, partial, st); break;
+    case RESIDUAL: launch_node64<Q, RESIDUAL>(lv, lv.all_nodes, (int)lv.n_int, u, out, f, partial, st); break;
     case SMOOTH:
       for (int cc = 0; cc < 4; ++cc)
         launch_node64<Q, SMOOTH>(lv, lv.colour_nodes + lv.colour_off[cc], lv.colour_off[cc + 1] - lv.colour_off[cc],
@@ -337,8 +385,8 @@ void launch_ifem(const LevelView<T>& lv, const uint32_t* list, int n, T* u, T* o
 template <class T>
 void ifem_all(const LevelView<T>& lv, Mode mode, T* u, T* out, const T* f, double* partial, cudaStream_t st) {
   switch (mode) {
-    case APPLY: launch_ifem<T, APPLY>(lv, lv.int_ijk, (int)lv.n_int, u, out, f, partial, st); break;
-    case RESIDUAL: launch_ifem<T, RESIDUAL>(lv, lv.int_ijk, (int)lv.n_int, u, out, f, partial, st); break;
+    case APPLY: launch_ifem<T, APPLY>(lv, lv.all_nodes, (int)lv.n_int, u, out, f, partial, st); break;
+    case RESIDUAL: launch_ifem<T, RESIDUAL>(lv, lv.all_nodes, (int)lv.n_int, u, out, f, partial, st); break;
     case SMOOTH:
       for (int cc = 0; cc < 4; ++cc)
         launch_ifem<T, SMOOTH>(lv, lv.colour_nodes + lv.colour_off[cc], lv.colour_off[cc + 1] - lv.colour_off[cc], u,

@@ -134,6 +134,44 @@ __device__ __forceinline__ T load_pt(const LevelView<T>& lv, const T* __restrict
   return lv.ghost[(int64_t)c * lv.n_full + lin_full(i, j, k, lv.N)];
 }
 
+// 32-bit position of an interior point among the cell's interior points
+// (same value as lin_interior; fits int32 for N <= 1024).
+__device__ __forceinline__ int lin_interior32(int i, int j, int k, int N) {
+  const int M = N - 4, a = i - 1, b = j - 1, c = k - 1, m = M - c;
+  auto tet = [](int n) { return (n + 1) * (n + 2) * (n + 3) / 6; };
+  return tet(M) - tet(M - c) + b * (m + 1) - b * (b - 1) / 2 + a;
+}
+
+// True when all 14 neighbours of interior point (i, j, k) are interior too.
+__device__ __forceinline__ bool deep_interior(int i, int j, int k, int N) {
+  return i >= 2 && j >= 2 && k >= 2 && i + j + k <= N - 2;
+}
+
+// Offsets (in interior positions) of the 14 neighbours of a deep-interior
+// point, DIRS order: with L = N-1-j-k the length of line (j, k) and
+// T(m) = m(m+1)/2 the size of an interior plane, tc = T(N-2-k) - j + 1 and
+// bc = -T(N-1-k) + j - 1; the others follow by +-1 and +-L.
+__device__ __forceinline__ void neighbour_offsets(int j, int k, int N, int off[14]) {
+  const int L = N - 1 - j - k;
+  const int m1 = N - 2 - k, m0 = N - 1 - k;
+  const int tc = m1 * (m1 + 1) / 2 - j + 1;
+  const int bc = -(m0 * (m0 + 1) / 2) + j - 1;
+  off[ME] = 1;
+  off[MW] = -1;
+  off[MN] = L;
+  off[MS] = -(L + 1);
+  off[MNW] = L - 1;
+  off[MSE] = -L;
+  off[TC] = tc;
+  off[TW] = tc - 1;
+  off[TS] = tc - L;
+  off[TSE] = tc - L + 1;
+  off[BC] = bc;
+  off[BE] = bc + 1;
+  off[BN] = bc + L + 1;
+  off[BNW] = bc + L;
+}
+
 // Sum over a block (blockDim.x a multiple of 32, at most 1024); result valid
 // in thread 0.
 __device__ __forceinline__ double block_sum(double v) {

@@ -45,7 +45,7 @@ struct LevelView {
   int64_t off_E, off_F, off_C, n_total, n_int, n_full;
   int n_bnd;
   const CellGeom* geom;          // [nC]
-  const uint32_t* plane_nodes;   // interior points (packed), ordered (k, colour, j, i)
+  const uint32_t* plane_nodes;   // interior points (packed) by (k, colour), deep-interior ones first
   const int* plane_off;          // start of (k, colour) in plane_nodes, [4 (N + 1) + 1]
   const uint32_t* int_ijk;       // [n_int] interior points in canonical order
   const uint32_t* bnd_ijk;       // [n_bnd] boundary points of a cell
@@ -59,7 +59,8 @@ struct LevelView {
   const long long* line64;
   const int* cell_e;             // [nC]
   int n_lines;                   // lines per cell, (N - 3)(N - 2) / 2
-  const uint32_t* colour_nodes;  // interior points (packed) ordered (colour, k, j, i)
+  const uint32_t* colour_nodes;  // interior points (packed) per colour, deep-interior ones first
+  const uint32_t* all_nodes;     // all interior points, deep-interior ones first
   int colour_off[5];             // start of each colour in colour_nodes
   // lower primitives: canonical rows 0 .. off_C-1 in sliced ELL (32-row
   // slices, column-major inside a slice), Dirichlet rows have diag 0
@@ -104,6 +105,7 @@ struct Level {
   long long* d_line64 = nullptr;
   int* d_cell_e = nullptr;
   uint32_t* d_colour_nodes = nullptr;
+  uint32_t* d_all_nodes = nullptr;
   int colour_off[5] = {0, 0, 0, 0, 0};
   // halo copies and work vectors (allocated on demand)
   double* d_ghost64 = nullptr;
