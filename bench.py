@@ -44,6 +44,8 @@ WORKLOADS = {
                                "N=64 intervals per macro edge, r in [0.55, 1]"),
     "shell3840_N128": (2, 4, 7, "3840 macro cells (icosahedral shell, 2 surface refinements, 4 layers), "
                                  "N=128 intervals per macro edge, r in [0.55, 1]"),
+    "shell1920_N64": (2, 2, 6, "1920 macro cells (icosahedral shell, 2 surface refinements, 2 layers), N=64, "
+                               "r in [0.55, 1]"),
     "shell480_N64": (1, 2, 6, "480 macro cells (icosahedral shell, 1 surface refinement, 2 layers), N=64, "
                               "r in [0.55, 1]"),
     "shell60_N16": (0, 1, 4, "60 macro cells (icosahedral shell, 1 layer), N=16, r in [0.55, 1]"),

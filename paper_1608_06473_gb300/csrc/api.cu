@@ -376,7 +376,7 @@ LevelView<float> view<float>(hhg_shell* s, int n) {
   v.n_total = d.n_total; v.n_int = d.n_int; v.n_full = d.n_full; v.n_bnd = d.n_bnd;
   v.geom = d.geom; v.plane_nodes = d.plane_nodes; v.plane_off = d.plane_off; v.int_ijk = d.int_ijk;
   v.bnd_ijk = d.bnd_ijk; v.bnd_slot = d.bnd_slot; v.halo_src = d.halo_src; v.ghost = L.d_ghost32;
-  v.coef = L.d_coef32; v.q = d.q;
+  v.coef = L.d_coef32; v.q = d.q; v.plane32 = L.d_plane32;
   v.colour_nodes = d.colour_nodes;
   v.all_nodes = d.all_nodes;
   for (int cc = 0; cc < 5; ++cc) v.colour_off[cc] = d.colour_off[cc];
@@ -609,7 +609,9 @@ static void fit(hhg_shell* s, int q, int j, cudaStream_t st) {
     const size_t ncoef = (size_t)L.lay.nC * 15 * mq;
     const size_t nline = (size_t)L.lay.nC * n_cell_lines(N) * line_rec(q);
     if (s->q != q || !L.d_coef) {  // (re)allocate only when the degree changes
-      for (void* p : {(void*)L.d_coef, (void*)L.d_coef32, (void*)L.d_line64, (void*)L.d_cell_e}) A.release(p);
+      for (void* p : {(void*)L.d_coef, (void*)L.d_coef32, (void*)L.d_line64, (void*)L.d_cell_e, (void*)L.d_plane32})
+        A.release(p);
+      L.d_plane32 = A.alloc_n<float>((size_t)plane_table_len((int)L.lay.nC, N, q));
       L.d_coef = A.alloc_n<double>(ncoef);
       L.d_coef32 = A.alloc_n<float>(ncoef);
       L.d_line64 = A.alloc_n<long long>(nline);
@@ -630,6 +632,7 @@ static void fit(hhg_shell* s, int q, int j, cudaStream_t st) {
                       st);
     }
     launch_line_table(v, q, L.d_coef, L.d_cell_e, L.d_line64, st);
+    launch_plane_table(v, q, L.d_coef, L.d_plane32, st);
     HHG_CUDA(cudaStreamSynchronize(st));
     A.release(d_b);
     A.release(d_pts);

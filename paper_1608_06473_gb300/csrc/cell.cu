@@ -30,6 +30,8 @@
 // closed-form 32-bit offsets within the cell's block of the canonical
 // vector; nodes next to the cell boundary read boundary neighbours from the
 // cell's halo copy.
+#include <cstdlib>
+
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -302,6 +304,73 @@ __global__ void __launch_bounds__(WAVE_THREADS, 2) lsqp_wave_kernel(LevelView<T>
   }
 }
 
+// FP32 per-plane table (fit time): for every cell, plane k = 1..N-3 and
+// direction, the (Q+1)(Q+2)/2 coefficients of the polynomial in (i, j),
+// formed in FP64 from the fitted coefficients and rounded once to FP32.
+template <int Q>
+__global__ void lsqp_plane_table_kernel(const double* __restrict__ coef, int nC, int N, float* __restrict__ table) {
+  constexpr int MQ = (Q + 1) * (Q + 2) * (Q + 3) / 6;
+  constexpr int NP = (Q + 1) * (Q + 2) / 2;
+  const int np = N - 3;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nC * np * 15) return;
+  const int w = (int)(t % 15);
+  const int64_t cp = t / 15;
+  const int c = (int)(cp / np), k = (int)(cp % np) + 1;
+  double P[NP];
+  plane_coeffs<double, Q>(coef + ((int64_t)c * 15 + w) * MQ, (double)k, P);
+  float* dst = table + t * NP;
+#pragma unroll
+  for (int a = 0; a < NP; ++a) dst[a] = (float)P[a];
+}
+
+// Per-plane coefficients of one direction padded to a multiple of 4 floats
+// (128-bit shared-memory loads).
+template <int Q>
+__host__ __device__ constexpr int np_pad() { return ((Q + 1) * (Q + 2) / 2 + 3) / 4 * 4; }
+
+template <int Q, Mode MODE>
+__global__ void __launch_bounds__(NODE_THREADS, 3) lsqp_node32_kernel(LevelView<float> lv,
+                                                                     const uint32_t* __restrict__ list, int n_list,
+                                                                     float* u, float* out, const float* f,
+                                                                     double* partial) {
+  constexpr int NP = (Q + 1) * (Q + 2) / 2;
+  constexpr int NPP = np_pad<Q>();
+  extern __shared__ __align__(16) float s_tab[];   // [N - 3][15][NPP]
+  const int c = blockIdx.x;
+  const int np = lv.N - 3;
+  const float* tab = lv.plane32 + (int64_t)c * np * 15 * NP;
+  for (int t = threadIdx.x; t < np * 15 * NPP; t += blockDim.x) {
+    const int e = t % NPP, pw = t / NPP;
+    s_tab[t] = e < NP ? tab[pw * NP + e] : 0.0f;
+  }
+  __syncthreads();
+  double nrm = 0.0;
+  for (int t = threadIdx.x; t < n_list; t += blockDim.x) {
+    const uint32_t p = list[t];
+    const int i = unpack_i(p), j = unpack_j(p), k = unpack_k(p);
+    const float* P = s_tab + (k - 1) * 15 * NPP;
+    const float ti = (float)i, tj = (float)j;
+    auto wt = [&](int w) -> float {
+      float Pw[NPP];
+#pragma unroll
+      for (int v = 0; v < NPP; v += 4) {
+        const float4 q4 = *reinterpret_cast<const float4*>(P + w * NPP + v);
+        Pw[v] = q4.x;
+        Pw[v + 1] = q4.y;
+        Pw[v + 2] = q4.z;
+        Pw[v + 3] = q4.w;
+      }
+      return eval_plane<float, Q>(Pw, ti, tj);
+    };
+    node_update<float, MODE>(lv, c, i, j, k, wt, u, out, f, nrm, 1.0f, 1.0f);
+  }
+  if (MODE == RESIDUAL) {
+    const double tot = block_sum(nrm);
+    if (threadIdx.x == 0) partial[c] = tot;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // IFEM: exact stencils assembled on the fly, thread per node
 // ---------------------------------------------------------------------------
@@ -359,6 +428,32 @@ void lsqp64(const LevelView<double>& lv, Mode mode, double* u, double* out, cons
     case SMOOTH:
       for (int cc = 0; cc < 4; ++cc)
         launch_node64<Q, SMOOTH>(lv, lv.colour_nodes + lv.colour_off[cc], lv.colour_off[cc + 1] - lv.colour_off[cc],
+                                 u, out, f, partial, st);
+      break;
+  }
+}
+
+template <int Q, Mode MODE>
+void launch_node32(const LevelView<float>& lv, const uint32_t* list, int n, float* u, float* out, const float* f,
+                   double* partial, cudaStream_t st) {
+  HHG_CHECK(lv.plane32 != nullptr, HHG_ENOTFIT, "FP32 surrogate plane table missing");
+  const size_t smem = sizeof(float) * (size_t)(lv.N - 3) * 15 * np_pad<Q>();
+  auto kern = lsqp_node32_kernel<Q, MODE>;
+  if (smem > 48 * 1024) HHG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<lv.nC, NODE_THREADS, smem, st>>>(lv, list, n, u, out, f, partial);
+  HHG_CUDA(cudaGetLastError());
+  count_launch();
+}
+
+template <int Q>
+void lsqp32(const LevelView<float>& lv, Mode mode, float* u, float* out, const float* f, double* partial,
+            cudaStream_t st) {
+  switch (mode) {
+    case APPLY: launch_node32<Q, APPLY>(lv, lv.all_nodes, (int)lv.n_int, u, out, f, partial, st); break;
+    case RESIDUAL: launch_node32<Q, RESIDUAL>(lv, lv.all_nodes, (int)lv.n_int, u, out, f, partial, st); break;
+    case SMOOTH:
+      for (int cc = 0; cc < 4; ++cc)
+        launch_node32<Q, SMOOTH>(lv, lv.colour_nodes + lv.colour_off[cc], lv.colour_off[cc + 1] - lv.colour_off[cc],
                                  u, out, f, partial, st);
       break;
   }
@@ -461,6 +556,16 @@ template <>
 void launch_cell<float>(const LevelView<float>& lv, int op, Mode mode, float* u, float* out, const float* f,
                         double* partial, cudaStream_t st) {
   if (lv.N < 4 || lv.n_int == 0) return;
+  static const bool wave = getenv("HHG_F32_WAVE") != nullptr;
+  if (op == HHG_OP_LSQP && lv.q > 0 && !wave) {
+    switch (lv.q) {
+      case 1: lsqp32<1>(lv, mode, u, out, f, partial, st); break;
+      case 2: lsqp32<2>(lv, mode, u, out, f, partial, st); break;
+      case 3: lsqp32<3>(lv, mode, u, out, f, partial, st); break;
+      default: throw Error{HHG_ENOTFIT, "surrogate degree not fitted"};
+    }
+    return;
+  }
   if (op == HHG_OP_LSQP && lv.q > 0) {
     switch (mode) {
       case APPLY: dispatch_wave<float, APPLY>(lv, u, out, f, partial, st); break;
@@ -494,6 +599,19 @@ void launch_line_table(const LevelView<double>& lv, int q, const double* coef, i
   }
   HHG_CUDA(cudaGetLastError());
   count_launch(2);
+}
+
+void launch_plane_table(const LevelView<double>& lv, int q, const double* coef, float* table, cudaStream_t st) {
+  const int64_t n = (int64_t)lv.nC * (lv.N - 3) * 15;
+  const unsigned g = (unsigned)((n + 127) / 128);
+  switch (q) {
+    case 1: lsqp_plane_table_kernel<1><<<g, 128, 0, st>>>(coef, lv.nC, lv.N, table); break;
+    case 2: lsqp_plane_table_kernel<2><<<g, 128, 0, st>>>(coef, lv.nC, lv.N, table); break;
+    case 3: lsqp_plane_table_kernel<3><<<g, 128, 0, st>>>(coef, lv.nC, lv.N, table); break;
+    default: throw Error{HHG_EINVAL, "q must be 1, 2 or 3"};
+  }
+  HHG_CUDA(cudaGetLastError());
+  count_launch();
 }
 
 void launch_sample(const LevelView<double>& lv, const uint32_t* pts, int n_pts, double* b, cudaStream_t st) {

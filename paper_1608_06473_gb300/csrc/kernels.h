@@ -35,6 +35,11 @@ void launch_cell<float>(const LevelView<float>& lv, int op, Mode mode, float* u,
 void launch_line_table(const LevelView<double>& lv, int q, const double* coef, int* cell_e, long long* table,
                        cudaStream_t st);
 
+// FP32 surrogate plane table (fit time): per cell, plane k and direction the
+// (q+1)(q+2)/2 coefficients of the polynomial in (i, j), rounded to FP32.
+void launch_plane_table(const LevelView<double>& lv, int q, const double* coef, float* table, cudaStream_t st);
+inline int64_t plane_table_len(int nC, int N, int q) { return (int64_t)nC * (N - 3) * 15 * ((q + 1) * (q + 2) / 2); }
+
 // Exact stencils (14 off-centre weights) at cell-local points of every cell:
 // b[(c * n_pts + p) * 14 + w] (Table 4.3 "t_sample").
 void launch_sample(const LevelView<double>& lv, const uint32_t* pts, int n_pts, double* b, cudaStream_t st);

@@ -59,6 +59,7 @@ struct LevelView {
   const long long* line64;
   const int* cell_e;             // [nC]
   int n_lines;                   // lines per cell, (N - 3)(N - 2) / 2
+  const float* plane32;          // FP32 surrogate: per cell, plane and direction the polynomial in (i, j)
   const uint32_t* colour_nodes;  // interior points (packed) per colour, deep-interior ones first
   const uint32_t* all_nodes;     // all interior points, deep-interior ones first
   int colour_off[5];             // start of each colour in colour_nodes
@@ -103,6 +104,7 @@ struct Level {
   double* d_coef = nullptr;
   float* d_coef32 = nullptr;
   long long* d_line64 = nullptr;
+  float* d_plane32 = nullptr;
   int* d_cell_e = nullptr;
   uint32_t* d_colour_nodes = nullptr;
   uint32_t* d_all_nodes = nullptr;
