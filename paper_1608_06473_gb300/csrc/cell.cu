@@ -330,7 +330,7 @@ template <int Q>
 __host__ __device__ constexpr int np_pad() { return ((Q + 1) * (Q + 2) / 2 + 3) / 4 * 4; }
 
 template <int Q, Mode MODE>
-__global__ void __launch_bounds__(NODE_THREADS, 3) lsqp_node32_kernel(LevelView<float> lv,
+__global__ void __launch_bounds__(NODE_THREADS, 4) lsqp_node32_kernel(LevelView<float> lv,
                                                                      const uint32_t* __restrict__ list, int n_list,
                                                                      float* u, float* out, const float* f,
                                                                      double* partial) {
