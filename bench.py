@@ -301,10 +301,11 @@ def run_ours(args, rank, world, local):
                     "peak_note": "FP64 nominal (recipe: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz)"}
     else:
         achieved = 12 * units_per_launch / avg_launch_s / 1e9
-        roofline = {"kernel": "lsqp_wave_kernel<float,%d,SMOOTH> (finest level, one launch per sweep)" % args.q,
+        roofline = {"kernel": "lsqp_stage32_smooth<%d> (finest level, one launch per sweep, planes staged in "
+                              "shared memory)" % args.q,
                     "bound": "hbm", "achieved": achieved, "peak": HBM_MEASURED_GBS, "unit": "GB/s",
                     "frac": achieved / HBM_MEASURED_GBS,
-                    "traffic": traffic_record("lsqp_wave_smooth_f32", args.workload),
+                    "traffic": traffic_record("lsqp_stage32_smooth", args.workload),
                     "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)"}
     roofline.update({"launches": sm_n, "avg_launch_ms": avg_launch_s * 1e3,
                      "algorithmic_flops_per_launch": flops,

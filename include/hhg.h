@@ -44,7 +44,10 @@
  *
  * Errors.  Every call returns an hhg_status; on failure hhg_last_error()
  * returns a message for the calling thread.  A CUDA error leaves the shell
- * usable only for hhg_destroy.
+ * usable only for hhg_destroy.  Kernels that stage data in shared memory
+ * wait on it with bounded waits; one that gives up sets a device error word
+ * that the next call waiting for the stream reports as HHG_ETIMEOUT (the
+ * results of the affected work are then undefined).
  *
  * Threads.  One shell may be used from one host thread at a time; calls on
  * the same shell that overlap on the GPU (different streams) race on its

@@ -338,6 +338,7 @@ LevelView<double> view<double>(hhg_shell* s, int n) {
   v.all_nodes = L.d_all_nodes;
   for (int cc = 0; cc < 5; ++cc) v.colour_off[cc] = L.colour_off[cc];
   v.sell_ptr = L.d_sell_ptr; v.sell_col = L.d_sell_col; v.sell_val = L.d_sell_val; v.low_diag = L.d_low_diag;
+  v.err = s->d_err;
   return v;
 }
 
@@ -381,6 +382,7 @@ LevelView<float> view<float>(hhg_shell* s, int n) {
   v.all_nodes = d.all_nodes;
   for (int cc = 0; cc < 5; ++cc) v.colour_off[cc] = d.colour_off[cc];
   v.sell_ptr = d.sell_ptr; v.sell_col = d.sell_col; v.sell_val = L.d_sell_val32; v.low_diag = L.d_low_diag32;
+  v.err = d.err;
   return v;
 }
 
@@ -473,6 +475,18 @@ static void op_smooth(hhg_shell* s, int n, int op, const T* f, T* u, cudaStream_
   launch_halo(v, (const T*)u, st);
   TimedScope ts(s, n, HHG_T_CELL_SMOOTH, st);
   launch_cell(v, eff_op(s, n, op), SMOOTH, u, u, f, nullptr, st);
+}
+
+// Reports (and clears) a bounded device-side wait that gave up since the
+// last check (the staged kernels set the shell's error word).
+static void check_device_error(hhg_shell* s, cudaStream_t st) {
+  int e = 0;
+  HHG_CUDA(cudaMemcpyAsync(&e, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  HHG_CUDA(cudaStreamSynchronize(st));
+  if (e != 0) {
+    HHG_CUDA(cudaMemsetAsync(s->d_err, 0, sizeof(int), st));
+    throw Error{HHG_ETIMEOUT, "a bounded device-side wait gave up (shared-memory staging did not complete)"};
+  }
 }
 
 static double read_scalar(hhg_shell* s, int slot, cudaStream_t st) {
@@ -779,6 +793,8 @@ hhg_status hhg_setup_shell(const hhg_shell_desc* d, void* stream, hhg_shell** ou
           geom[c].r[a] = s->mesh.vr[v];
         }
       s->d_geom = upload(s->alloc, geom, st);
+      s->d_err = s->alloc.alloc_n<int>(4);
+      HHG_CUDA(cudaMemsetAsync(s->d_err, 0, 4 * sizeof(int), st));
       s->levels.resize(s->Lf - 1);
       for (int n = 0; n < (int)s->levels.size(); ++n) build_level(s, n, st);
       // reduction scratch: 64 scalar slots, then partial sums (per-cell and
@@ -928,6 +944,7 @@ hhg_status hhg_smooth(hhg_shell* s, int L, hhg_op op, hhg_dtype dtype, const voi
         launch_zero_list(Lv.d_dirichlet, Lv.n_dirichlet, au.dev32(), st);
         for (int t = 0; t < sweeps; ++t) op_smooth<float>(s, n, op, af.dev32(), au.dev32(), st);
         stage_out(au, nt, st);
+        if (au.host) check_device_error(s, st);
         continue;
       }
       Arg af = stage_in(s, 1, (const double*)f + b * nt, nt, true, st);
@@ -974,6 +991,7 @@ hhg_status hhg_vcycle(hhg_shell* s, hhg_op op, hhg_dtype dtype, const void* f, v
         }
         op_residual(s, n, op, au.dev, af.dev, Lv.d_r, 10, st);
         const double rn = std::sqrt(read_scalar(s, 10, st));
+        check_device_error(s, st);
         HHG_CHECK(std::isfinite(rn), HHG_EDIVERGED, "residual norm became NaN or Inf");
         rel = rn / r0;
         ++cyc;

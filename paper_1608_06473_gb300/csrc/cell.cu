@@ -11,17 +11,15 @@
 //    (lsqp_line_table_kernel) as integers scaled by 2^E (E per cell, chosen so
 //    every partial sum stays below 2^62) and kept in HBM.  Per node the
 //    polynomial is evaluated exactly by integer Horner and converted to FP64
-//    once per weight; the FP64 pipe then only carries the conversions, the 14
-//    stencil products and the divide.  Kernels are thread-per-node with one
-//    CTA per macro cell and no barriers; the smoother is one launch per colour.
-//  * FP32: one CTA per cell walks its planes; per plane k each direction's
-//    polynomial is reduced to a polynomial in (i, j) in shared memory and
-//    evaluated per node (FP32 arithmetic is cheap, HBM traffic is the
-//    bound), and the four colours run in one launch as a plane wavefront:
-//    in step s colour c is updated on plane s + 1 - c, c = 0..3, with a
-//    barrier after each colour, so every update sees all lower-colour updates
-//    of planes k - 1, k, k + 1 and none of the higher ones -- exactly four
-//    colour sweeps in one pass over the cell.
+//    on the integer pipe; the FP64 pipe carries only the 14 stencil products,
+//    the scaling and a Newton-Raphson divide.  Kernels are thread-per-node
+//    with one CTA per macro cell and no barriers; the smoother is one launch
+//    per colour.
+//  * FP32: per plane k each direction's polynomial is reduced to a
+//    polynomial in (i, j) at fit time (FP32 table) and evaluated per node
+//    from shared memory.  The smoother stages the cell's planes in shared
+//    memory and runs the four colours in one launch (stage.cu); apply and
+//    residual are thread-per-node kernels here.
 //
 // IFEM (Sec. 4.2.1): every node assembles its 15 weights from the 24 element
 // matrices around it (thread per node, one launch per colour).
@@ -30,8 +28,6 @@
 // closed-form 32-bit offsets within the cell's block of the canonical
 // vector; nodes next to the cell boundary read boundary neighbours from the
 // cell's halo copy.
-#include <cstdlib>
-
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -41,8 +37,10 @@ namespace hhg {
 
 namespace {
 
-constexpr int WAVE_THREADS = 256;  // FP32 wavefront kernel
 constexpr int NODE_THREADS = 256;  // thread-per-node kernels
+// FP32 smoother: shared-memory staged one-launch sweep (stage.cu) instead of
+// four colour launches of the thread-per-node kernel.
+constexpr bool kStagedSmoother = false;
 
 // Coefficients of the polynomial in i along line (j, k): c_a(j, k) =
 // sum_{b,d} A_{a,b,d} j^b k^d.  Storage order of A (per direction):
@@ -173,6 +171,116 @@ __global__ void lsqp_line_table_kernel(const double* __restrict__ coef, const in
   for (int r = 15 * (Q + 1); r < line_rec(Q); ++r) dst[r] = 0;
 }
 
+// v * i + c (mod 2^64) for a 32-bit multiplier i >= 0: the low word times i
+// widened to 64 bits plus c, then the high word times i added to the top
+// half (two integer multiply-adds instead of a full 64 x 64 product).
+__device__ __forceinline__ long long mad_i64_u32(long long v, unsigned i, long long c) {
+  const unsigned long long vu = (unsigned long long)v;
+  unsigned long long r = (unsigned long long)(unsigned)vu * i + (unsigned long long)c;
+  r += (unsigned long long)((unsigned)(vu >> 32) * i) << 32;
+  return (long long)r;
+}
+
+// Line polynomial C_Q i^Q + ... + C_0 in exact integer arithmetic (Horner).
+template <int Q>
+__device__ __forceinline__ long long horner_i64(const long long* C, unsigned i) {
+  long long v = C[Q];
+#pragma unroll
+  for (int a = Q - 1; a >= 0; --a) v = mad_i64_u32(v, i, C[a]);
+  return v;
+}
+
+// int64 -> FP64 on the integer pipe (GB300 issues FP64 conversions on its
+// narrow FP64 pipe): magnitude, leading-zero count, normalising shift, and
+// the biased exponent added to the top bits, where the leading one of the
+// shifted magnitude carries into the exponent field.  The mantissa is
+// truncated toward zero (relative error below 2^-52); 0 maps to +0.
+__device__ __forceinline__ double i64_to_f64(long long v) {
+  const unsigned long long sign = (unsigned long long)v & 0x8000000000000000ull;
+  const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const int lz = __clzll((long long)a);
+  unsigned long long m;
+  asm("shl.b64 %0, %1, %2;" : "=l"(m) : "l"(a), "r"(lz));  // PTX clamps a shift of 64 to 0
+  const unsigned long long bits = ((unsigned long long)(1085 - lz) << 52) + (m >> 11);
+  return a ? __longlong_as_double((long long)(bits | sign)) : 0.0;
+}
+
+// n / d for normal d: the hardware reciprocal estimate refined by two
+// Newton-Raphson steps x <- x + x (1 - d x) (each squares the relative error),
+// the last one folded into the product: n x (1 + e) with e = 1 - d x.  The
+// result is within a few ulp of the correctly rounded quotient, at 5 FP64
+// operations instead of the longer IEEE division sequence.
+__device__ __forceinline__ double div_nr(double n, double d) {
+  double x;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(d));
+  double e = fma(-d, x, 1.0);
+  x = fma(x, e, x);
+  e = fma(-d, x, 1.0);
+  const double t = n * x;
+  return fma(t, e, t);
+}
+
+// One interior node of the FP64 surrogate.  C is the line record of (j, k):
+// 15 polynomials in i of degree Q, Q + 1 int64 each, scaled by 2^E.  Weights
+// are formed in pairs (w, w + 1) from 16-byte loads (the pair starts at an
+// even int64 offset) and converted on the integer pipe; the FP64 pipe
+// carries only the 14 products, the scaling and the divide.
+template <int Q, Mode MODE, class NB>
+__device__ __forceinline__ void lsqp64_node(const long long* __restrict__ C, unsigned i, NB nb, int64_t I, double* u,
+                                            double* out, const double* f, double& nrm, double scale,
+                                            double inv_scale) {
+  auto pair = [&](int w, double& a, double& b) {
+    long long r[2 * (Q + 1)];
+    const longlong2* p2 = reinterpret_cast<const longlong2*>(C + w * (Q + 1));
+#pragma unroll
+    for (int h = 0; h < Q + 1; ++h) {
+      const longlong2 x = __ldg(p2 + h);
+      r[2 * h] = x.x;
+      r[2 * h + 1] = x.y;
+    }
+    a = i64_to_f64(horner_i64<Q>(r, i));
+    b = i64_to_f64(horner_i64<Q>(r + Q + 1, i));
+  };
+  auto centre = [&]() {
+    long long r[Q + 2];
+    const longlong2* p2 = reinterpret_cast<const longlong2*>(C + MC * (Q + 1));
+#pragma unroll
+    for (int h = 0; h < (Q + 2) / 2; ++h) {
+      const longlong2 x = __ldg(p2 + h);
+      r[2 * h] = x.x;
+      r[2 * h + 1] = x.y;
+    }
+    return i64_to_f64(horner_i64<Q>(r, i));
+  };
+  if (MODE == SMOOTH) {
+    double acc = f[I] * scale;
+#pragma unroll
+    for (int w = 0; w < 14; w += 2) {
+      double a, b;
+      pair(w, a, b);
+      acc = fma(-a, nb(w), acc);
+      acc = fma(-b, nb(w + 1), acc);
+    }
+    u[I] = div_nr(acc, centre());
+  } else {
+    double y = centre() * u[I];
+#pragma unroll
+    for (int w = 0; w < 14; w += 2) {
+      double a, b;
+      pair(w, a, b);
+      y = fma(a, nb(w), y);
+      y = fma(b, nb(w + 1), y);
+    }
+    if (MODE == APPLY) {
+      out[I] = y * inv_scale;
+    } else {
+      const double r = fma(-inv_scale, y, f[I]);
+      out[I] = r;
+      nrm = fma(r, r, nrm);
+    }
+  }
+}
+
 template <int Q, Mode MODE>
 __global__ void __launch_bounds__(NODE_THREADS, 3) lsqp_node_kernel(LevelView<double> lv, const uint32_t* __restrict__ list,
                                                                   int n_list, double* u, double* out, const double* f,
@@ -182,18 +290,23 @@ __global__ void __launch_bounds__(NODE_THREADS, 3) lsqp_node_kernel(LevelView<do
   const int E = lv.cell_e[c];
   const double scale = ldexp(1.0, E), inv_scale = ldexp(1.0, -E);
   const long long* tab = lv.line64 + (int64_t)c * lv.n_lines * line_rec(Q);
+  const int64_t base = lv.off_C + (int64_t)c * lv.n_int;
   double nrm = 0.0;
   for (int t = threadIdx.x; t < n_list; t += blockDim.x) {
     const uint32_t p = list[t];
     const int i = unpack_i(p), j = unpack_j(p), k = unpack_k(p);
     const long long* C = tab + (int64_t)line_id(j, k, N) * line_rec(Q);
-    auto wt = [&](int w) -> double {
-      long long v = C[w * (Q + 1) + Q];
-#pragma unroll
-      for (int a = Q - 1; a >= 0; --a) v = v * (long long)i + C[w * (Q + 1) + a];
-      return (double)v;
-    };
-    node_update<double, MODE>(lv, c, i, j, k, wt, u, out, f, nrm, scale, inv_scale);
+    const int64_t I = base + lin_interior32(i, j, k, N);
+    if (deep_interior(i, j, k, N)) {
+      int off[14];
+      neighbour_offsets(j, k, N, off);
+      const double* pu = u + I;
+      lsqp64_node<Q, MODE>(C, (unsigned)i, [&](int w) { return pu[off[w]]; }, I, u, out, f, nrm, scale, inv_scale);
+    } else {
+      lsqp64_node<Q, MODE>(C, (unsigned)i,
+                           [&](int w) { return load_pt(lv, (const double*)u, c, i + DI(w), j + DJ(w), k + DK(w)); },
+                           I, u, out, f, nrm, scale, inv_scale);
+    }
   }
   if (MODE == RESIDUAL) {
     const double tot = block_sum(nrm);
@@ -202,107 +315,8 @@ __global__ void __launch_bounds__(NODE_THREADS, 3) lsqp_node_kernel(LevelView<do
 }
 
 // ---------------------------------------------------------------------------
-// FP32 surrogate: plane wavefront, per-plane polynomials in (i, j)
+// FP32 surrogate: per-plane polynomials in (i, j), thread per node
 // ---------------------------------------------------------------------------
-
-// Index of A_{a,b,d} (coefficient of i^a j^b k^d) in the storage order
-// for a = 0..Q, for d = 0..Q-a, for b = 0..Q-a-d.
-template <int Q>
-__host__ __device__ constexpr int coef_index(int a, int b, int d) {
-  int t = 0;
-  for (int aa = 0; aa < a; ++aa) t += (Q - aa + 1) * (Q - aa + 2) / 2;
-  for (int dd = 0; dd < d; ++dd) t += Q - a - dd + 1;
-  return t + b;
-}
-// Per plane and direction: D_{a,b}(k) = sum_d A_{a,b,d} k^d, stored for
-// a = 0..Q, b = 0..Q-a; (Q+1)(Q+2)/2 values.
-template <int Q>
-__host__ __device__ constexpr int plane_index(int a, int b) {
-  int t = 0;
-  for (int aa = 0; aa < a; ++aa) t += Q - aa + 1;
-  return t + b;
-}
-
-template <class T, int Q>
-__device__ __forceinline__ void plane_coeffs(const T* A, T k, T* P) {
-#pragma unroll
-  for (int a = 0; a <= Q; ++a)
-#pragma unroll
-    for (int b = 0; b <= Q - a; ++b) {
-      T v = A[coef_index<Q>(a, b, Q - a - b)];
-#pragma unroll
-      for (int d = Q - a - b - 1; d >= 0; --d) v = fma(v, k, A[coef_index<Q>(a, b, d)]);
-      P[plane_index<Q>(a, b)] = v;
-    }
-}
-
-template <class T, int Q>
-__device__ __forceinline__ T eval_plane(const T* P, T i, T j) {
-  T s = 0;
-#pragma unroll
-  for (int a = Q; a >= 0; --a) {
-    T c = P[plane_index<Q>(a, Q - a)];
-#pragma unroll
-    for (int b = Q - a - 1; b >= 0; --b) c = fma(c, j, P[plane_index<Q>(a, b)]);
-    s = (a == Q) ? c : fma(s, i, c);
-  }
-  return s;
-}
-
-template <class T, int Q, Mode MODE>
-__global__ void __launch_bounds__(WAVE_THREADS, 2) lsqp_wave_kernel(LevelView<T> lv, T* u, T* out, const T* f,
-                                                                 double* partial) {
-  constexpr int MQ = (Q + 1) * (Q + 2) * (Q + 3) / 6;
-  constexpr int NP = (Q + 1) * (Q + 2) / 2;       // per-plane values per direction
-  constexpr int NSLOT = (MODE == SMOOTH) ? 4 : 1;
-  __shared__ T sA[15 * MQ];
-  __shared__ T ring[NSLOT][15 * NP];
-  const int c = blockIdx.x;
-  const int N = lv.N;
-  for (int t = threadIdx.x; t < 15 * MQ; t += blockDim.x) sA[t] = lv.coef[(int64_t)c * 15 * MQ + t];
-  __syncthreads();
-  double nrm = 0.0;
-
-  auto prologue = [&](int k) {
-    const int slot = (NSLOT == 4) ? (k & 3) : 0;
-    if (threadIdx.x < 15) plane_coeffs<T, Q>(sA + threadIdx.x * MQ, (T)k, &ring[slot][threadIdx.x * NP]);
-  };
-  auto process = [&](int k, int beg, int end) {
-    const int slot = (NSLOT == 4) ? (k & 3) : 0;
-    for (int t = beg + threadIdx.x; t < end; t += blockDim.x) {
-      const uint32_t p = lv.plane_nodes[t];
-      const int i = unpack_i(p), j = unpack_j(p);
-      const T* P = ring[slot];
-      const T ti = (T)i, tj = (T)j;
-      auto wt = [&](int w) -> T { return eval_plane<T, Q>(P + w * NP, ti, tj); };
-      node_update<T, MODE>(lv, c, i, j, k, wt, u, out, f, nrm, T(1), T(1));
-    }
-  };
-
-  if (MODE == SMOOTH) {
-    for (int s = 0; s <= N - 1; ++s) {
-      if (s + 1 <= N - 3) prologue(s + 1);
-      __syncthreads();
-#pragma unroll 1
-      for (int cc = 0; cc < 4; ++cc) {
-        const int k = s + 1 - cc;
-        if (k >= 1 && k <= N - 3) process(k, lv.plane_off[k * 4 + cc], lv.plane_off[k * 4 + cc + 1]);
-        __syncthreads();
-      }
-    }
-  } else {
-    for (int k = 1; k <= N - 3; ++k) {
-      prologue(k);
-      __syncthreads();
-      process(k, lv.plane_off[k * 4], lv.plane_off[k * 4 + 4]);
-      __syncthreads();
-    }
-  }
-  if (MODE == RESIDUAL) {
-    const double tot = block_sum(nrm);
-    if (threadIdx.x == 0) partial[c] = tot;
-  }
-}
 
 // FP32 per-plane table (fit time): for every cell, plane k = 1..N-3 and
 // direction, the (Q+1)(Q+2)/2 coefficients of the polynomial in (i, j),
@@ -323,11 +337,6 @@ __global__ void lsqp_plane_table_kernel(const double* __restrict__ coef, int nC,
 #pragma unroll
   for (int a = 0; a < NP; ++a) dst[a] = (float)P[a];
 }
-
-// Per-plane coefficients of one direction padded to a multiple of 4 floats
-// (128-bit shared-memory loads).
-template <int Q>
-__host__ __device__ constexpr int np_pad() { return ((Q + 1) * (Q + 2) / 2 + 3) / 4 * 4; }
 
 template <int Q, Mode MODE>
 __global__ void __launch_bounds__(NODE_THREADS, 4) lsqp_node32_kernel(LevelView<float> lv,
@@ -403,13 +412,6 @@ __global__ void __launch_bounds__(NODE_THREADS) ifem_node_kernel(LevelView<T> lv
 // launchers
 // ---------------------------------------------------------------------------
 
-template <class T, int Q, Mode MODE>
-void launch_wave(const LevelView<T>& lv, T* u, T* out, const T* f, double* partial, cudaStream_t st) {
-  lsqp_wave_kernel<T, Q, MODE><<<lv.nC, WAVE_THREADS, 0, st>>>(lv, u, out, f, partial);
-  HHG_CUDA(cudaGetLastError());
-  count_launch();
-}
-
 template <int Q, Mode MODE>
 void launch_node64(const LevelView<double>& lv, const uint32_t* list, int n, double* u, double* out, const double* f,
                    double* partial, cudaStream_t st) {
@@ -456,16 +458,6 @@ void lsqp32(const LevelView<float>& lv, Mode mode, float* u, float* out, const f
         launch_node32<Q, SMOOTH>(lv, lv.colour_nodes + lv.colour_off[cc], lv.colour_off[cc + 1] - lv.colour_off[cc],
                                  u, out, f, partial, st);
       break;
-  }
-}
-
-template <class T, Mode MODE>
-void dispatch_wave(const LevelView<T>& lv, T* u, T* out, const T* f, double* partial, cudaStream_t st) {
-  switch (lv.q) {
-    case 1: launch_wave<T, 1, MODE>(lv, u, out, f, partial, st); break;
-    case 2: launch_wave<T, 2, MODE>(lv, u, out, f, partial, st); break;
-    case 3: launch_wave<T, 3, MODE>(lv, u, out, f, partial, st); break;
-    default: throw Error{HHG_ENOTFIT, "surrogate degree not fitted"};
   }
 }
 
@@ -556,21 +548,16 @@ template <>
 void launch_cell<float>(const LevelView<float>& lv, int op, Mode mode, float* u, float* out, const float* f,
                         double* partial, cudaStream_t st) {
   if (lv.N < 4 || lv.n_int == 0) return;
-  static const bool wave = getenv("HHG_F32_WAVE") != nullptr;
-  if (op == HHG_OP_LSQP && lv.q > 0 && !wave) {
+  if (op == HHG_OP_LSQP && lv.q > 0) {
+    if (mode == SMOOTH && kStagedSmoother && stage32_supported(lv, u)) {
+      launch_stage32_smooth(lv, u, f, st);
+      return;
+    }
     switch (lv.q) {
       case 1: lsqp32<1>(lv, mode, u, out, f, partial, st); break;
       case 2: lsqp32<2>(lv, mode, u, out, f, partial, st); break;
       case 3: lsqp32<3>(lv, mode, u, out, f, partial, st); break;
       default: throw Error{HHG_ENOTFIT, "surrogate degree not fitted"};
-    }
-    return;
-  }
-  if (op == HHG_OP_LSQP && lv.q > 0) {
-    switch (mode) {
-      case APPLY: dispatch_wave<float, APPLY>(lv, u, out, f, partial, st); break;
-      case RESIDUAL: dispatch_wave<float, RESIDUAL>(lv, u, out, f, partial, st); break;
-      case SMOOTH: dispatch_wave<float, SMOOTH>(lv, u, out, f, partial, st); break;
     }
     return;
   }

@@ -191,4 +191,55 @@ __device__ __forceinline__ double block_sum(double v) {
   return v;
 }
 
+// ---- FP32 surrogate: per-plane polynomials in (i, j) ----------------------
+
+// Index of A_{a,b,d} (coefficient of i^a j^b k^d) in the storage order
+// for a = 0..Q, for d = 0..Q-a, for b = 0..Q-a-d.
+template <int Q>
+__host__ __device__ constexpr int coef_index(int a, int b, int d) {
+  int t = 0;
+  for (int aa = 0; aa < a; ++aa) t += (Q - aa + 1) * (Q - aa + 2) / 2;
+  for (int dd = 0; dd < d; ++dd) t += Q - a - dd + 1;
+  return t + b;
+}
+// Per plane and direction: D_{a,b}(k) = sum_d A_{a,b,d} k^d, stored for
+// a = 0..Q, b = 0..Q-a; (Q+1)(Q+2)/2 values.
+template <int Q>
+__host__ __device__ constexpr int plane_index(int a, int b) {
+  int t = 0;
+  for (int aa = 0; aa < a; ++aa) t += Q - aa + 1;
+  return t + b;
+}
+
+template <class T, int Q>
+__device__ __forceinline__ void plane_coeffs(const T* A, T k, T* P) {
+#pragma unroll
+  for (int a = 0; a <= Q; ++a)
+#pragma unroll
+    for (int b = 0; b <= Q - a; ++b) {
+      T v = A[coef_index<Q>(a, b, Q - a - b)];
+#pragma unroll
+      for (int d = Q - a - b - 1; d >= 0; --d) v = fma(v, k, A[coef_index<Q>(a, b, d)]);
+      P[plane_index<Q>(a, b)] = v;
+    }
+}
+
+template <class T, int Q>
+__device__ __forceinline__ T eval_plane(const T* P, T i, T j) {
+  T s = 0;
+#pragma unroll
+  for (int a = Q; a >= 0; --a) {
+    T c = P[plane_index<Q>(a, Q - a)];
+#pragma unroll
+    for (int b = Q - a - 1; b >= 0; --b) c = fma(c, j, P[plane_index<Q>(a, b)]);
+    s = (a == Q) ? c : fma(s, i, c);
+  }
+  return s;
+}
+
+// Per-plane coefficients of one direction padded to a multiple of 4 floats
+// (128-bit shared-memory loads).
+template <int Q>
+__host__ __device__ constexpr int np_pad() { return ((Q + 1) * (Q + 2) / 2 + 3) / 4 * 4; }
+
 }  // namespace hhg

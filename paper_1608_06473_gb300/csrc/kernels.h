@@ -29,6 +29,13 @@ template <>
 void launch_cell<float>(const LevelView<float>& lv, int op, Mode mode, float* u, float* out, const float* f,
                         double* partial, cudaStream_t st);
 
+// FP32 surrogate smoother with shared-memory plane staging (stage.cu): the
+// four cell colour steps in one launch per sweep.  Supported when the
+// surrogate is fitted, u is 16-byte aligned and the plane ring fits in
+// shared memory; a bounded wait that gives up sets *lv.err.
+bool stage32_supported(const LevelView<float>& lv, const float* u);
+void launch_stage32_smooth(const LevelView<float>& lv, float* u, const float* f, cudaStream_t st);
+
 // FP64 surrogate line table (fit time): per cell the scale exponent E and,
 // per line (j, k), the q+1 coefficients of each of the 15 polynomials in i,
 // times 2^E, rounded to int64.

@@ -69,6 +69,7 @@ struct LevelView {
   const int* sell_col;           // canonical column, -1 = padding
   const T* sell_val;
   const T* low_diag;             // [off_C]
+  int* err;                      // device error word: set to 1 when a bounded wait gives up
 };
 
 struct Level {
@@ -146,6 +147,7 @@ struct hhg_shell {
   double* d_red = nullptr;             // reduction scratch (partials + results)
   int64_t red_len = 0;
   double* d_cg = nullptr;              // coarse-solver vectors
+  int* d_err = nullptr;                // device error word of the staged kernels (0 = ok)
   void* coarse_op = nullptr;           // hhg::CoarseOp of the N = 4 level (owned)
   double* d_stage[3] = {nullptr, nullptr, nullptr};  // staging for host-pointer arguments
   bool f32_ready = false;              // FP32 resources allocated
