@@ -66,12 +66,17 @@ def parse():
     p.add_argument("--j", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--mode", choices=["solve", "smoother"], default="solve",
+    p.add_argument("--mode", choices=["solve", "smoother", "serve"], default="solve",
                    help="solve: the whole path per step (default); smoother: finest-level sweeps only "
                         "(for profiling the smoother kernels)")
     p.add_argument("--op", choices=["lsqp", "ifem"], default="lsqp", help="operator for --mode smoother")
+    p.add_argument("--smooth-cfg", type=int, default=None,
+                   help="--mode smoother, mixed precision: pin the FP32 smoother configuration of the finest "
+                        "level (-1 per-colour kernel, 0..3 staged; default: the tuner's choice)")
     p.add_argument("--precision", choices=["f64", "mixed"], default="f64",
                    help="f64: FP64 V-cycles; mixed: FP32 V-cycles inside FP64 iterative refinement")
+    p.add_argument("--serve-requests", type=int, default=48,
+                   help="requests of the serving stream reported beside the solve (0 = skip)")
     p.add_argument("--compare-f64", action="store_true",
                    help="with --precision mixed: also time one plain FP64 solve and report the speedup")
     return p.parse_args()
@@ -301,8 +306,11 @@ def run_ours(args, rank, world, local):
                     "peak_note": "FP64 nominal (recipe: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz)"}
     else:
         achieved = 12 * units_per_launch / avg_launch_s / 1e9
-        roofline = {"kernel": "lsqp_stage32_smooth<%d> (finest level, one launch per sweep, planes staged in "
-                              "shared memory)" % args.q,
+        cfg = hhg.hhg_tuning(s.handle, L)[0]
+        kname = ("lsqp_stage32_smooth<%d> (finest level, one launch per sweep, planes staged in shared memory; "
+                 "tuned configuration %d)" % (args.q, cfg)) if cfg >= 0 else \
+            "lsqp_node32_kernel<%d,SMOOTH> (finest level, tuned: one launch per colour)" % args.q
+        roofline = {"kernel": kname,
                     "bound": "hbm", "achieved": achieved, "peak": HBM_MEASURED_GBS, "unit": "GB/s",
                     "frac": achieved / HBM_MEASURED_GBS,
                     "traffic": traffic_record("lsqp_stage32_smooth", args.workload),
@@ -325,6 +333,8 @@ def run_ours(args, rank, world, local):
            "smoother_glups": {"lsqp": g_lsqp, "ifem": g_ifem, "lsqp_over_ifem": g_lsqp / g_ifem},
            "vcycle_s_to_1e-8": ms * 1e-3 / args.steps, "cycles": cyc_list, "final_relres": max(rels),
            "breakdown": breakdown, "f64_solve": f64_solve,
+           "smoother_tuning": ({str(l): hhg.hhg_tuning(s.handle, l)[0] for l in range(3, L + 1)}
+                               if args.precision == "mixed" else None),
            "speedup_over_f64_solve": (f64_solve["s"] / (ms * 1e-3 / args.steps)) if f64_solve else None}
     s.close()
     return out
@@ -390,6 +400,71 @@ def run_reference(args, rank, world):
             "e2e": {"value": v, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+SERVE_RADII = [0.35 + 0.05 * k for k in range(8)]   # inner radii of the request stream (8-point grid)
+SERVE_LEVELS = [4, 5, 6, 7]                          # N = 16 .. 128 on the 60-macro shell
+
+
+def serve_run(n_requests, rate_hz=200.0, seed=2024, max_inflight=4, warm=True):
+    """Poisson stream of shell solves through the library's request loop
+    (hhg_server_*): levels 4-7 and inner radius (from an 8-point grid in
+    [0.35, 0.7]) drawn uniformly, 1-8 right-hand sides uniform[-1, 1] each,
+    mixed precision to relative residual 1e-8.  With warm=True every
+    (radius, level) hierarchy is built once before the timed stream, so the
+    stream measures the resident-hierarchy steady state.  Returns latency
+    percentiles and throughput from the library's own per-request stamps."""
+    import paper_1608_06473_gb300 as hhg
+    import synthetic
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gaps = rng.exponential(1.0 / rate_hz, n_requests)
+    reqs = [(float(SERVE_RADII[rng.integers(8)]), int(SERVE_LEVELS[rng.integers(4)]), int(rng.integers(1, 9)))
+            for _ in range(n_requests)]
+    pool = {}   # right-hand sides per level (the vector length depends on the level only): 8 seeded vectors
+
+    def rhs(ri, L, nr):
+        if L not in pool:
+            n, _ = hhg.hhg_problem_nodes(ri, 1.0, 0, 1, L)
+            pool[L] = np.stack([synthetic.uniform(n, 900 + b) for b in range(8)])
+        return pool[L][:nr]
+
+    srv = hhg.Server(max_inflight=max_inflight, dtype=hhg.HHG_F32, rtol=1e-8)
+    try:
+        if warm:
+            ts = [srv.submit(rhs(ri, L, 1), r_inner=ri, L=L) for ri in SERVE_RADII for L in SERVE_LEVELS]
+            for t in ts:
+                srv.wait(t)
+        for ri, L, nr in reqs:
+            rhs(ri, L, nr)
+        t0 = time.perf_counter()
+        tickets = []
+        for (ri, L, nr), g in zip(reqs, gaps):
+            t0 += g
+            dt = t0 - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(srv.submit(rhs(ri, L, nr), r_inner=ri, L=L))
+        infos, worst = [], 0.0
+        for t in tickets:
+            _, rel, info = srv.wait(t)
+            worst = max(worst, float(rel.max()))
+            infos.append(info)
+        stats = srv.stats()
+    finally:
+        srv.close()
+    lat = np.array([i["t_end"] - i["t_submit"] for i in infos])
+    span = max(i["t_end"] for i in infos) - min(i["t_submit"] for i in infos)
+    n_rhs = sum(nr for _, _, nr in reqs)
+    return {"requests": n_requests, "arrival_rate_hz": rate_hz, "max_inflight": max_inflight,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "mean_latency_s": float(lat.mean()), "throughput_req_s": n_requests / span,
+            "throughput_rhs_s": n_rhs / span, "worst_relres": worst,
+            "reused": int(sum(i["reused"] for i in infos)), "resident_hierarchies": stats["resident"],
+            "resident_gb": stats["bytes"] / 1e9,
+            "workload": "Poisson arrivals (mean %g req/s) of shell solves on the 60-macro icosahedral shell, "
+                        "levels 4-7 (N=16..128) and r_inner in {0.35,0.40,...,0.70} drawn uniformly, 1-8 "
+                        "right-hand sides uniform[-1,1]; mixed precision, V(3,3) to 1e-8; hierarchies "
+                        "resident (built before the stream)" % rate_hz}
+
+
 def run_smoother(args):
     """Finest-level smoother only: setup, fit, `warmup` sweeps, then `steps`
     sweeps timed with CUDA events on the launching stream."""
@@ -408,6 +483,9 @@ def run_smoother(args):
     dtype = hhg.HHG_F32 if args.precision == "mixed" else hhg.HHG_F64
     f = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_F)).cuda().to(dt)
     u = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_U)).cuda().to(dt)
+    if args.smooth_cfg is not None and args.precision == "mixed":
+        s.smooth(f, u.clone(), 1, op=opcode, dtype=dtype, stream=stream)   # allocates and tunes the FP32 buffers
+        hhg.hhg_set_tuning(s.handle, L, args.smooth_cfg)
     s.smooth(f, u, args.warmup, op=opcode, dtype=dtype, stream=stream)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -416,8 +494,10 @@ def run_smoother(args):
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
+    tuning = hhg.hhg_tuning(s.handle, L) if args.precision == "mixed" else None
     s.close()
     return {"mode": "smoother", "op": args.op, "precision": "f32" if args.precision == "mixed" else "f64",
+            "tuning": None if tuning is None else {"cfg": tuning[0], "ms": list(tuning[1])},
             "workload": args.workload, "sweeps": args.steps,
             "ms_per_sweep": ms / args.steps, "GLUP/s": n_free * args.steps / (ms * 1e-3) / 1e9}
 
@@ -426,6 +506,9 @@ def main():
     args = parse()
     if args.mode == "smoother":
         print(json.dumps(run_smoother(args)))
+        return
+    if args.mode == "serve":
+        print(json.dumps(serve_run(args.serve_requests)))
         return
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))
@@ -436,6 +519,8 @@ def main():
         return
     rank, world, local = dist_init(args.gpus)
     out = run_ours(args, rank, world, local)
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        out["serving"] = serve_run(args.serve_requests)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.workload)

@@ -166,6 +166,84 @@ hhg_status hhg_vcycle(hhg_shell* shell, hhg_op op, hhg_dtype dtype,
                       double rtol, int nrhs, double* relres_out, int* cycles_out,
                       void* stream);
 
+/* CUDA graphs in hhg_vcycle (enable != 0, the default): the first cycle of
+ * a call runs launch by launch and its coarsest solve sets an iteration
+ * count; every later cycle replays one CUDA graph of the whole V-cycle
+ * (captured once per vector pointers, batch size and cycle parameters, and
+ * again after a fit or tuning change), on a stream of the shell ordered
+ * after `stream` by events.  Inside the graph the coarsest solve runs that
+ * fixed number of conjugate-gradient iterations, each leaving converged
+ * right-hand sides unchanged; should it stop short of the tolerance the
+ * cycle's correction is kept and the next capture doubles the count.
+ * enable = 0 runs every cycle launch by launch. */
+hhg_status hhg_set_graphs(hhg_shell* shell, int enable);
+
+/* ---- Serving: a request loop over resident hierarchies -----------------
+ * Not a construct of the paper: a solve service for streams of shell
+ * problems.  Requests (a shell geometry, a level, 1..n right-hand sides) are
+ * queued by hhg_server_submit and admitted in arrival order as soon as one
+ * of `max_inflight` slots is free and the request fits the HBM budget.  A
+ * request runs on its slot's own CUDA stream and host worker thread, so
+ * admitted requests overlap on the device.  Hierarchies (index maps, halo
+ * copies, pre-assembled lower-primitive rows) and their surrogate
+ * coefficients stay resident in a cache keyed by the geometry and level;
+ * a request reuses an idle cached hierarchy of its key, else a new one is
+ * built and fitted, evicting idle hierarchies (least recently used first)
+ * when the budget requires.  Each request is solved by the batched V-cycle
+ * (all of its right-hand sides together, as hhg_vcycle with device vectors)
+ * to the server's tolerance; its result does not depend on what else is in
+ * flight (every kernel and reduction has a fixed order; only the FP32
+ * smoother configuration, chosen per hierarchy by timing, may change the
+ * rounding of mixed-precision solves). */
+typedef struct hhg_server hhg_server;
+
+typedef struct {
+  size_t hbm_budget_bytes;  /* resident hierarchies + request vectors; 0 = no limit */
+  int max_inflight;         /* concurrent requests (slots), >= 1 */
+  int q, j;                 /* surrogate degree and sampling (hhg_fit_surrogate) */
+  int nu1, nu2;             /* V(nu1, nu2) */
+  int max_cycles;
+  double rtol;              /* stop at ||r|| <= rtol ||r0|| for every right-hand side */
+  hhg_dtype dtype;          /* HHG_F64 or HHG_F32 (mixed precision, see hhg_vcycle) */
+} hhg_server_desc;
+
+/* One request's geometry and level (as hhg_shell_desc; L = fine_log2_intervals). */
+typedef struct {
+  double r_inner, r_outer;
+  int tang_refine, radial_layers, L;
+} hhg_problem;
+
+/* Per-request record: times in seconds since the server was created. */
+typedef struct {
+  double t_submit, t_start, t_end;
+  int cycles;               /* V-cycles run */
+  int reused;               /* 1 if a resident hierarchy served it, 0 if one was built */
+  hhg_status status;
+} hhg_request_info;
+
+/* Vector length and unknown count of a problem (no GPU work). */
+hhg_status hhg_problem_nodes(const hhg_problem* p, int64_t* n_total, int64_t* n_free);
+
+hhg_status hhg_server_create(const hhg_server_desc* desc, hhg_server** out);
+
+/* Queues a request; f_host holds nrhs vectors of hhg_problem_nodes' n_total
+ * doubles (copied before return).  *ticket identifies it. */
+hhg_status hhg_server_submit(hhg_server* srv, const hhg_problem* p, const double* f_host, int nrhs,
+                             int64_t* ticket);
+
+/* Waits for a request; copies its solutions (nrhs vectors) to u_host and the
+ * final relative residuals to relres (both nullable) and returns the
+ * request's own status (HHG_ENOCONV, HHG_ENOMEM when it can never fit the
+ * budget, ...).  A ticket can be waited for once. */
+hhg_status hhg_server_wait(hhg_server* srv, int64_t ticket, double* u_host, double* relres,
+                           hhg_request_info* info);
+
+/* Resident hierarchies and their bytes (diagnostics). */
+hhg_status hhg_server_stats(hhg_server* srv, int* n_resident, size_t* bytes_resident, int64_t* n_built);
+
+/* Waits for every queued request, then frees all hierarchies. */
+hhg_status hhg_server_destroy(hhg_server* srv);
+
 /* ---- Residual without allocation (no counterpart in the paper) ----------
  * Some callers cannot allocate device memory at the moment they need a
  * residual: code in a latency-critical loop that must not stall on the
@@ -219,6 +297,21 @@ typedef enum {
  * HHG_T_COARSE: the number of conjugate-gradient iterations). */
 hhg_status hhg_timing(hhg_shell* shell, int enable);
 hhg_status hhg_timing_read(hhg_shell* shell, int which, double* total_ms, int64_t* launches);
+
+/* Launch configuration the tuner chose for the FP32 surrogate smoother on
+ * level L (the tuner times the candidates on the device once the FP32
+ * buffers exist and after every fit): *cfg = -1 for the per-colour
+ * thread-per-node kernel, 0..3 for the shared-memory staged one-launch
+ * kernel with (wavefront skew, threads per CTA) = (1, 256), (1, 1024),
+ * (2, 128), (2, 512); -2 if not tuned.  ms (nullable, 5 entries) receives
+ * each candidate's best time for one cell sweep (-1 = not run). */
+hhg_status hhg_tuning(const hhg_shell* shell, int L, int* cfg, double* ms);
+
+/* Pins the FP32 surrogate smoother of level L to configuration cfg (-1 or a
+ * staged configuration 0..3 as above) until the next fit; a staged
+ * configuration that does not fit the level falls back to the per-colour
+ * kernel at launch.  HHG_EINVAL for an unknown cfg. */
+hhg_status hhg_set_tuning(hhg_shell* shell, int L, int cfg);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* hhg_last_error(void);

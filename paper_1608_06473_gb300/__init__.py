@@ -52,6 +52,22 @@ class hhg_shell_desc(ctypes.Structure):
                 ("hbm_budget_bytes", ctypes.c_size_t)]
 
 
+class hhg_server_desc(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int), ("q", ctypes.c_int),
+                ("j", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_cycles", ctypes.c_int),
+                ("rtol", ctypes.c_double), ("dtype", ctypes.c_int)]
+
+
+class hhg_problem(ctypes.Structure):
+    _fields_ = [("r_inner", ctypes.c_double), ("r_outer", ctypes.c_double), ("tang_refine", ctypes.c_int),
+                ("radial_layers", ctypes.c_int), ("L", ctypes.c_int)]
+
+
+class hhg_request_info(ctypes.Structure):
+    _fields_ = [("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_end", ctypes.c_double),
+                ("cycles", ctypes.c_int), ("reused", ctypes.c_int), ("status", ctypes.c_int)]
+
+
 _lib = None
 
 _P = ctypes.c_void_p
@@ -67,7 +83,18 @@ _SIGS = {
     "hhg_smooth": [_P, _I, _I, _I, _P, _P, _I, _I, _P],
     "hhg_vcycle": [_P, _I, _I, _P, _P, _I, _I, _I, ctypes.c_double, _I, _P, _P, _P],
     "hhg_residual_noalloc": [_P, _I, _I, _P, _P, _P, _P, _P],
+    "hhg_problem_nodes": [ctypes.POINTER(hhg_problem), ctypes.POINTER(ctypes.c_int64),
+                          ctypes.POINTER(ctypes.c_int64)],
+    "hhg_server_create": [ctypes.POINTER(hhg_server_desc), ctypes.POINTER(_P)],
+    "hhg_server_submit": [_P, ctypes.POINTER(hhg_problem), _P, _I, ctypes.POINTER(ctypes.c_int64)],
+    "hhg_server_wait": [_P, ctypes.c_int64, _P, _P, ctypes.POINTER(hhg_request_info)],
+    "hhg_server_stats": [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t),
+                         ctypes.POINTER(ctypes.c_int64)],
+    "hhg_server_destroy": [_P],
     "hhg_timing": [_P, _I],
+    "hhg_tuning": [_P, _I, ctypes.POINTER(ctypes.c_int), _P],
+    "hhg_set_tuning": [_P, _I, _I],
+    "hhg_set_graphs": [_P, _I],
     "hhg_timing_read": [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
 }
 
@@ -115,6 +142,22 @@ def hhg_timing_read(shell: int, which: int):
     ms, n = ctypes.c_double(), ctypes.c_int64()
     _check(lib().hhg_timing_read(shell, which, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def hhg_tuning(shell: int, L: int):
+    """(chosen FP32 smoother configuration, per-candidate ms) of level L."""
+    cfg = ctypes.c_int()
+    ms = np.zeros(5)
+    _check(lib().hhg_tuning(shell, L, ctypes.byref(cfg), ms.ctypes.data))
+    return cfg.value, ms
+
+
+def hhg_set_graphs(shell: int, enable: bool):
+    _check(lib().hhg_set_graphs(shell, int(bool(enable))))
+
+
+def hhg_set_tuning(shell: int, L: int, cfg: int):
+    _check(lib().hhg_set_tuning(shell, L, cfg))
 
 
 def hhg_last_error() -> str:
@@ -269,3 +312,67 @@ class Shell:
     def vcycle(self, f, u, nu1=3, nu2=3, max_cycles=50, rtol=1e-8, op=HHG_OP_LSQP, dtype=HHG_F64, nrhs=1,
                stream=None, raise_on_noconv=True):
         return hhg_vcycle(self.handle, op, dtype, f, u, nu1, nu2, max_cycles, rtol, nrhs, stream, raise_on_noconv)
+
+
+def hhg_problem_nodes(r_inner, r_outer, tang_refine, radial_layers, L):
+    """(n_total, n_free) of a shell problem (no GPU work)."""
+    p = hhg_problem(r_inner, r_outer, tang_refine, radial_layers, L)
+    nt, nf = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().hhg_problem_nodes(ctypes.byref(p), ctypes.byref(nt), ctypes.byref(nf)))
+    return nt.value, nf.value
+
+
+class Server:
+    """Solve service over resident hierarchies (hhg_server_* of include/hhg.h):
+    submit() queues a shell problem with its right-hand sides (host arrays,
+    copied), wait() returns (u, relres, info) once it is solved."""
+
+    def __init__(self, hbm_budget_bytes=0, max_inflight=4, q=2, j=2, nu1=3, nu2=3, max_cycles=60, rtol=1e-8,
+                 dtype=HHG_F32):
+        d = hhg_server_desc(hbm_budget_bytes, max_inflight, q, j, nu1, nu2, max_cycles, rtol, dtype)
+        h = ctypes.c_void_p()
+        _check(lib().hhg_server_create(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h.value
+        self._shapes = {}
+
+    def submit(self, f, r_inner=0.55, r_outer=1.0, tang_refine=0, radial_layers=1, L=4) -> int:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        nrhs = 1 if f.ndim == 1 else f.shape[0]
+        p = hhg_problem(r_inner, r_outer, tang_refine, radial_layers, L)
+        t = ctypes.c_int64()
+        _check(lib().hhg_server_submit(self.handle, ctypes.byref(p), f.ctypes.data, nrhs, ctypes.byref(t)))
+        self._shapes[t.value] = (nrhs, f.shape[-1])
+        return t.value
+
+    def wait(self, ticket, raise_on_error=True):
+        nrhs, n = self._shapes.pop(ticket)
+        u = np.empty((nrhs, n))
+        rel = np.empty(nrhs)
+        info = hhg_request_info()
+        st = lib().hhg_server_wait(self.handle, ticket, u.ctypes.data, rel.ctypes.data, ctypes.byref(info))
+        if st != HHG_OK and raise_on_error:
+            raise HHGError(st, hhg_last_error())
+        return u, rel, {"t_submit": info.t_submit, "t_start": info.t_start, "t_end": info.t_end,
+                        "cycles": info.cycles, "reused": bool(info.reused), "status": info.status}
+
+    def stats(self):
+        n, b, built = ctypes.c_int(), ctypes.c_size_t(), ctypes.c_int64()
+        _check(lib().hhg_server_stats(self.handle, ctypes.byref(n), ctypes.byref(b), ctypes.byref(built)))
+        return {"resident": n.value, "bytes": b.value, "built": built.value}
+
+    def close(self):
+        if self.handle:
+            _check(lib().hhg_server_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

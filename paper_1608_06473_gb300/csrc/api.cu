@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -29,6 +30,22 @@ static thread_local std::string g_last_error;
 static std::atomic<int64_t> g_launches{0};
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+void ensure_smem_limit(const void* func, size_t bytes) {
+  if (bytes <= 48 * 1024) return;
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, size_t>> enabled;
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto& e : enabled)
+    if (e.first == func) {
+      if (e.second >= bytes) return;
+      HHG_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+      e.second = bytes;
+      return;
+    }
+  HHG_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  enabled.push_back({func, bytes});
+}
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void* Allocator::alloc(size_t bytes) {
@@ -64,6 +81,8 @@ void Allocator::release_all() {
   live.clear();
   used = 0;
 }
+
+static void check_device_error(hhg_shell* s, cudaStream_t st);
 
 template <class T>
 static T* upload(Allocator& A, const std::vector<T>& h, cudaStream_t st) {
@@ -146,6 +165,27 @@ static void build_level(hhg_shell* s, int n, cudaStream_t st) {
               plane_nodes.push_back(pack_ijk(i, j, k));
     }
   plane_off[4 * (N + 1)] = (int)plane_nodes.size();
+  // for the staged smoother: each listed point's position within its plane
+  // (interior points of plane k, line by line), and for points next to the
+  // cell boundary the 14 neighbour codes, [w][entry]: bit 31 set = halo
+  // point (low bits: its cell-local full index), else bits 29-30 = dk + 1
+  // and the low bits the neighbour's position within plane k + dk
+  const int n_plane = (int)plane_nodes.size();
+  std::vector<int> plane_x((size_t)n_plane), plane_nb((size_t)14 * n_plane, 0);
+  for (int e = 0; e < n_plane; ++e) {
+    const uint32_t p = plane_nodes[e];
+    const int i = unpack_i(p), j = unpack_j(p), k = unpack_k(p);
+    plane_x[e] = (int)(lin_interior(i, j, k, N) - lin_interior(1, 1, k, N));
+    if (deep(i, j, k)) continue;
+    for (int w = 0; w < 14; ++w) {
+      const int i2 = i + dir_di(w), j2 = j + dir_dj(w), k2 = k + dir_dk(w);
+      plane_nb[(size_t)w * n_plane + e] =
+          is_interior(i2, j2, k2, N)
+              ? (int)(((uint32_t)(dir_dk(w) + 1) << 29) |
+                      (uint32_t)(lin_interior(i2, j2, k2, N) - lin_interior(1, 1, k2, N)))
+              : (int)(0x80000000u | (uint32_t)lin_full(i2, j2, k2, N));
+    }
+  }
   std::vector<uint32_t> int_ijk;
   for (int k = 1; k < N; ++k)
     for (int j = 1; j < N - k; ++j)
@@ -224,6 +264,9 @@ static void build_level(hhg_shell* s, int n, cudaStream_t st) {
   L.d_dirichlet = upload(A, dirl, st);
 
   L.d_plane_nodes = upload(A, plane_nodes, st);
+  L.d_plane_x = upload(A, plane_x, st);
+  L.d_plane_nb = upload(A, plane_nb, st);
+  L.n_plane = n_plane;
   L.d_plane_off = upload(A, plane_off, st);
   L.d_int_ijk = upload(A, int_ijk, st);
   L.d_colour_nodes = upload(A, colour_nodes, st);
@@ -331,6 +374,7 @@ LevelView<double> view<double>(hhg_shell* s, int n) {
   v.N = L.N; v.nC = (int)lay.nC; v.off_E = lay.off_E; v.off_F = lay.off_F; v.off_C = lay.off_C;
   v.n_total = lay.n_total; v.n_int = lay.n_int; v.n_full = lay.n_full; v.n_bnd = L.n_bnd;
   v.geom = s->d_geom; v.plane_nodes = L.d_plane_nodes; v.plane_off = L.d_plane_off; v.int_ijk = L.d_int_ijk;
+  v.plane_x = L.d_plane_x; v.plane_nb = L.d_plane_nb; v.n_plane = L.n_plane;
   v.bnd_ijk = L.d_bnd_ijk; v.bnd_slot = L.d_bnd_slot; v.halo_src = L.d_halo_src; v.ghost = L.d_ghost64;
   v.coef = L.d_coef; v.q = (L.d_coef && L.N >= 8) ? s->q : 0;
   v.line64 = L.d_line64; v.cell_e = L.d_cell_e; v.n_lines = (int)n_cell_lines(L.N);
@@ -339,33 +383,12 @@ LevelView<double> view<double>(hhg_shell* s, int n) {
   for (int cc = 0; cc < 5; ++cc) v.colour_off[cc] = L.colour_off[cc];
   v.sell_ptr = L.d_sell_ptr; v.sell_col = L.d_sell_col; v.sell_val = L.d_sell_val; v.low_diag = L.d_low_diag;
   v.err = s->d_err;
+  v.nrhs = s->nb;
+  v.vstride = lay.n_total;
+  v.gstride = lay.nC * lay.n_full;
+  v.pstride = s->pstride;
+  v.tstride = std::max(L.max_step, 1);
   return v;
-}
-
-// FP32 buffers of every level, allocated on the first FP32 call: halo
-// copies, work vectors and FP32 copies of the lower-primitive rows.
-static void ensure_f32(hhg_shell* s, cudaStream_t st) {
-  if (s->f32_ready) return;
-  Allocator& A = s->alloc;
-  for (auto& L : s->levels) {
-    const LevelLayout& lay = L.lay;
-    L.d_ghost32 = A.alloc_n<float>((size_t)(lay.nC * lay.n_full));
-    HHG_CUDA(cudaMemsetAsync(L.d_ghost32, 0, sizeof(float) * lay.nC * lay.n_full, st));
-    for (float** v : {&L.d_u32, &L.d_f32, &L.d_r32}) {
-      *v = A.alloc_n<float>((size_t)lay.n_total);
-      HHG_CUDA(cudaMemsetAsync(*v, 0, sizeof(float) * lay.n_total, st));
-    }
-    L.d_tmp32 = A.alloc_n<float>((size_t)std::max(L.max_step, 1));
-    int64_t nsell = 0;
-    HHG_CUDA(cudaMemcpyAsync(&nsell, L.d_sell_ptr + L.n_slices, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    HHG_CUDA(cudaStreamSynchronize(st));
-    L.d_sell_val32 = A.alloc_n<float>((size_t)std::max<int64_t>(nsell, 1));
-    L.d_low_diag32 = A.alloc_n<float>((size_t)std::max<int64_t>(lay.off_C, 1));
-    launch_copy_cast<float>(L.d_sell_val, L.d_sell_val32, nsell, st);
-    launch_copy_cast<float>(L.d_low_diag, L.d_low_diag32, lay.off_C, st);
-  }
-  HHG_CUDA(cudaStreamSynchronize(st));
-  s->f32_ready = true;
 }
 
 template <>
@@ -376,6 +399,7 @@ LevelView<float> view<float>(hhg_shell* s, int n) {
   v.N = d.N; v.nC = d.nC; v.off_E = d.off_E; v.off_F = d.off_F; v.off_C = d.off_C;
   v.n_total = d.n_total; v.n_int = d.n_int; v.n_full = d.n_full; v.n_bnd = d.n_bnd;
   v.geom = d.geom; v.plane_nodes = d.plane_nodes; v.plane_off = d.plane_off; v.int_ijk = d.int_ijk;
+  v.plane_x = d.plane_x; v.plane_nb = d.plane_nb; v.n_plane = d.n_plane;
   v.bnd_ijk = d.bnd_ijk; v.bnd_slot = d.bnd_slot; v.halo_src = d.halo_src; v.ghost = L.d_ghost32;
   v.coef = L.d_coef32; v.q = d.q; v.plane32 = L.d_plane32;
   v.colour_nodes = d.colour_nodes;
@@ -383,7 +407,94 @@ LevelView<float> view<float>(hhg_shell* s, int n) {
   for (int cc = 0; cc < 5; ++cc) v.colour_off[cc] = d.colour_off[cc];
   v.sell_ptr = d.sell_ptr; v.sell_col = d.sell_col; v.sell_val = L.d_sell_val32; v.low_diag = L.d_low_diag32;
   v.err = d.err;
+  v.smooth_cfg = L.tune32 >= 0 ? L.tune32 : -1;
+  v.nrhs = d.nrhs;
+  v.vstride = d.vstride;
+  v.gstride = d.gstride;
+  v.pstride = d.pstride;
+  v.tstride = d.tstride;
   return v;
+}
+
+// Tuner of the FP32 surrogate smoother: on every fitted level, times the
+// per-colour node kernel and each staged configuration that fits (one
+// warm-up and three timed cell sweeps each, CUDA events on `st`, on the
+// level's own FP32 work vectors) and keeps the fastest.  Runs once the FP32
+// buffers exist and again after every fit.
+static void tune_smooth32(hhg_shell* s, cudaStream_t st) {
+  if (!s->f32_ready || s->q == 0) return;
+  cudaEvent_t e0, e1;
+  HHG_CUDA(cudaEventCreate(&e0));
+  HHG_CUDA(cudaEventCreate(&e1));
+  for (size_t n = 0; n < s->levels.size(); ++n) {
+    Level& L = s->levels[n];
+    if (L.N < 8) continue;
+    LevelView<float> v = view<float>(s, (int)n);
+    v.nrhs = 1;
+    float best_ms = 0.0f;
+    int best = -1;
+    for (int cfg = -1; cfg < STAGE32_CONFIGS; ++cfg) {
+      L.tune32_ms[cfg + 1] = -1.0;
+      if (cfg >= 0 && !stage32_supported(v, L.d_u32, cfg)) continue;
+      v.smooth_cfg = cfg;
+      launch_cell(v, HHG_OP_LSQP, SMOOTH, L.d_u32, L.d_u32, (const float*)L.d_f32, nullptr, st);
+      float ms = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        HHG_CUDA(cudaEventRecord(e0, st));
+        launch_cell(v, HHG_OP_LSQP, SMOOTH, L.d_u32, L.d_u32, (const float*)L.d_f32, nullptr, st);
+        HHG_CUDA(cudaEventRecord(e1, st));
+        HHG_CUDA(cudaEventSynchronize(e1));
+        float t = 0.0f;
+        HHG_CUDA(cudaEventElapsedTime(&t, e0, e1));
+        ms = std::min(ms, t);
+      }
+      L.tune32_ms[cfg + 1] = ms;
+      if (best_ms == 0.0f || ms < best_ms) {
+        best_ms = ms;
+        best = cfg;
+      }
+    }
+    L.tune32 = best;
+  }
+  ++s->gen;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // the timed sweeps ran on the work vectors: clear them again
+  for (auto& L : s->levels) {
+    HHG_CUDA(cudaMemsetAsync(L.d_u32, 0, sizeof(float) * L.lay.n_total, st));
+    HHG_CUDA(cudaMemsetAsync(L.d_f32, 0, sizeof(float) * L.lay.n_total, st));
+  }
+  HHG_CUDA(cudaStreamSynchronize(st));
+  check_device_error(s, st);
+}
+
+// FP32 buffers of every level, allocated on the first FP32 call: halo
+// copies, work vectors and FP32 copies of the lower-primitive rows.
+static void ensure_f32(hhg_shell* s, cudaStream_t st) {
+  if (s->f32_ready) return;
+  Allocator& A = s->alloc;
+  const int64_t cap = s->cap;
+  for (auto& L : s->levels) {
+    const LevelLayout& lay = L.lay;
+    L.d_ghost32 = A.alloc_n<float>((size_t)(cap * lay.nC * lay.n_full));
+    HHG_CUDA(cudaMemsetAsync(L.d_ghost32, 0, sizeof(float) * cap * lay.nC * lay.n_full, st));
+    for (float** v : {&L.d_u32, &L.d_f32, &L.d_r32}) {
+      *v = A.alloc_n<float>((size_t)(cap * lay.n_total));
+      HHG_CUDA(cudaMemsetAsync(*v, 0, sizeof(float) * cap * lay.n_total, st));
+    }
+    L.d_tmp32 = A.alloc_n<float>((size_t)(cap * std::max(L.max_step, 1)));
+    int64_t nsell = 0;
+    HHG_CUDA(cudaMemcpyAsync(&nsell, L.d_sell_ptr + L.n_slices, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    HHG_CUDA(cudaStreamSynchronize(st));
+    L.d_sell_val32 = A.alloc_n<float>((size_t)std::max<int64_t>(nsell, 1));
+    L.d_low_diag32 = A.alloc_n<float>((size_t)std::max<int64_t>(lay.off_C, 1));
+    launch_copy_cast<float>(L.d_sell_val, L.d_sell_val32, nsell, st);
+    launch_copy_cast<float>(L.d_low_diag, L.d_low_diag32, lay.off_C, st);
+  }
+  HHG_CUDA(cudaStreamSynchronize(st));
+  s->f32_ready = true;
+  ++s->gen;
+  tune_smooth32(s, st);
 }
 
 template <class T>
@@ -412,12 +523,37 @@ struct TimedScope {
   ~TimedScope() {
     if (!b) return;
     cudaEventRecord(e, st);
-    s->tevents[which].push_back({b, e});
+    if (s->capturing) s->gtimed.emplace_back(which, b, e);  // an event-record node pair of the graph
+    else s->tevents[which].push_back({b, e});
   }
 };
 
+static void graph_timed_clear(hhg_shell* s) {
+  for (auto& t : s->gtimed) {
+    cudaEventDestroy(std::get<1>(t));
+    cudaEventDestroy(std::get<2>(t));
+  }
+  s->gtimed.clear();
+}
+
+// After a graph replay has completed: adds its timed scopes to the totals.
+static void graph_timed_accumulate(hhg_shell* s) {
+  if (!s->timing) return;
+  for (auto& t : s->gtimed) {
+    float ms = 0;
+    HHG_CUDA(cudaEventElapsedTime(&ms, std::get<1>(t), std::get<2>(t)));
+    s->gsum[std::get<0>(t)] += ms;
+    s->gcnt[std::get<0>(t)] += 1;
+  }
+  s->cg_iters += s->cg_graph_iters;  // the replayed cycle's coarse solve
+}
+
 static void timing_clear(hhg_shell* s) {
   s->cg_iters = 0;
+  for (int t = 0; t < HHG_T_COUNT; ++t) {
+    s->gsum[t] = 0.0;
+    s->gcnt[t] = 0;
+  }
   for (auto& v : s->tevents) {
     for (auto& p : v) {
       cudaEventDestroy(p.first);
@@ -450,20 +586,26 @@ static void op_apply(hhg_shell* s, int n, int op, const T* u, T* y, cudaStream_t
   launch_low(v, APPLY, u, y, (const T*)nullptr, nullptr, low_blocks(v.off_C), st);
 }
 
-// r = f - L u; the squared norm lands in d_red[slot] (device).
+// Reduction scratch: 64 scalar slots of `cap` entries (slot k, right-hand
+// side b at d_red[k cap + b]), then `cap` blocks of pstride partial sums.
+static double* scal(hhg_shell* s, int slot) { return s->d_red + (int64_t)slot * s->cap; }
+static double* parts(hhg_shell* s) { return s->d_red + 64 * (int64_t)s->cap; }
+
+// r = f - L u for the active right-hand sides; the squared norms land in
+// scalar slot `slot` (device).
 template <class T = double>
 static void op_residual(hhg_shell* s, int n, int op, const T* u, const T* f, T* r, int slot, cudaStream_t st) {
   TimedScope all(s, -1, HHG_T_RESIDUAL, st);
   LevelView<T> v = view<T>(s, n);
   const int nb = low_blocks(v.off_C);
-  double* part = s->d_red + 64;
+  double* part = parts(s);
   launch_halo(v, u, st);
   {
     TimedScope ts(s, n, HHG_T_CELL_RESIDUAL, st);
     launch_cell(v, eff_op(s, n, op), RESIDUAL, const_cast<T*>(u), r, f, part, st);
   }
   launch_low(v, RESIDUAL, u, r, f, part + v.nC, nb, st);
-  launch_sum(part, v.nC + nb, s->d_red + slot, st);
+  launch_sum(part, v.nC + nb, v.nrhs, v.pstride, scal(s, slot), st);
 }
 
 template <class T = double>
@@ -479,19 +621,27 @@ static void op_smooth(hhg_shell* s, int n, int op, const T* f, T* u, cudaStream_
 
 // Reports (and clears) a bounded device-side wait that gave up since the
 // last check (the staged kernels set the shell's error word).
+// Word 1 of the error word is soft: a coarse solve inside a captured
+// V-cycle stopped at its fixed iteration count before the tolerance; the
+// next capture doubles the count (the cycle's correction is still valid).
 static void check_device_error(hhg_shell* s, cudaStream_t st) {
-  int e = 0;
-  HHG_CUDA(cudaMemcpyAsync(&e, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  int e[2] = {0, 0};
+  HHG_CUDA(cudaMemcpyAsync(e, s->d_err, sizeof(e), cudaMemcpyDeviceToHost, st));
   HHG_CUDA(cudaStreamSynchronize(st));
-  if (e != 0) {
+  if (e[1] != 0) {
+    HHG_CUDA(cudaMemsetAsync(s->d_err + 1, 0, sizeof(int), st));
+    s->cg_graph_iters *= 2;
+  }
+  if (e[0] != 0) {
     HHG_CUDA(cudaMemsetAsync(s->d_err, 0, sizeof(int), st));
     throw Error{HHG_ETIMEOUT, "a bounded device-side wait gave up (shared-memory staging did not complete)"};
   }
 }
 
-static double read_scalar(hhg_shell* s, int slot, cudaStream_t st) {
-  double h = 0;
-  HHG_CUDA(cudaMemcpyAsync(&h, s->d_red + slot, sizeof(double), cudaMemcpyDeviceToHost, st));
+// The active right-hand sides' entries of a scalar slot (waits for the stream).
+static std::vector<double> read_scalars(hhg_shell* s, int slot, cudaStream_t st) {
+  std::vector<double> h((size_t)s->nb);
+  HHG_CUDA(cudaMemcpyAsync(h.data(), scal(s, slot), sizeof(double) * s->nb, cudaMemcpyDeviceToHost, st));
   HHG_CUDA(cudaStreamSynchronize(st));
   return h;
 }
@@ -503,24 +653,43 @@ static double read_scalar(hhg_shell* s, int slot, cudaStream_t st) {
 static void coarse_solve(hhg_shell* s, const double* f, double* x, cudaStream_t st) {
   TimedScope all(s, -1, HHG_T_COARSE, st);
   const CoarseOp& A = *static_cast<CoarseOp*>(s->coarse_op);
-  const int64_t n = A.n_total;
+  const int64_t n = A.n_total, cap = s->cap;
   double* r = s->d_cg;
-  double* z = r + n;
-  double* p = z + n;
-  double* q = p + n;
-  double* part = s->d_red + 64;
-  // scalar slots: 0, 1 = r.z (double-buffered), 2 = r.r, 3 = r0.r0
-  launch_cg_init(A, f, x, r, z, p, part, s->d_red + 0, s->d_red + 3, st);
-  const double ff = read_scalar(s, 3, st);
-  if (ff == 0.0) return;
-  const double tol2 = 1e-26 * ff;
+  double* z = r + n * cap;
+  double* p = z + n * cap;
+  double* q = p + n * cap;
+  double* part = parts(s);  // 3 CG_BLOCKS partials per right-hand side (pstride >= 3 CG_BLOCKS)
+  // scalar slots: 0, 1 = r.z (double-buffered), 2 = r.r, 3 = r0.r0,
+  // 4, 5 = r.r double-buffered for fixed-count iterations
+  launch_cg_init(A, f, x, r, z, p, part, scal(s, 0), scal(s, 3), s->nb, st);
+  if (s->cg_fixed > 0) {
+    // no host reads (inside a graph): a fixed number of iterations, each
+    // skipping the right-hand sides that have converged
+    HHG_CUDA(cudaMemcpyAsync(scal(s, 4), scal(s, 3), sizeof(double) * s->nb, cudaMemcpyDeviceToDevice, st));
+    for (int it = 0; it < s->cg_fixed; ++it)
+      launch_cg_iteration(A, x, r, z, p, q, part, scal(s, it & 1), scal(s, (it + 1) & 1), scal(s, 4 + ((it + 1) & 1)),
+                          s->nb, st, scal(s, 4 + (it & 1)), scal(s, 3));
+    launch_cg_check(scal(s, 4 + (s->cg_fixed & 1)), scal(s, 3), s->nb, s->d_err + 1, st);
+    return;
+  }
+  const std::vector<double> ff = read_scalars(s, 3, st);
+  bool zero = true;
+  for (double v : ff) zero = zero && v == 0.0;
+  if (zero) return;
   for (int it = 0; it < 20000; ++it) {
     ++s->cg_iters;
-    launch_cg_iteration(A, x, r, z, p, q, part, s->d_red + (it & 1), s->d_red + ((it + 1) & 1), s->d_red + 2, st);
+    launch_cg_iteration(A, x, r, z, p, q, part, scal(s, it & 1), scal(s, (it + 1) & 1), scal(s, 2), s->nb, st);
     if ((it & 7) == 7) {
-      const double rr = read_scalar(s, 2, st);
-      if (!std::isfinite(rr)) throw Error{HHG_EDIVERGED, "coarse solve diverged"};
-      if (rr <= tol2) return;
+      const std::vector<double> rr = read_scalars(s, 2, st);
+      bool done = true;
+      for (int b = 0; b < s->nb; ++b) {
+        if (!std::isfinite(rr[b])) throw Error{HHG_EDIVERGED, "coarse solve diverged"};
+        done = done && rr[b] <= 1e-26 * ff[b];
+      }
+      if (done) {
+        s->cg_last = it + 1;
+        return;
+      }
     }
   }
   throw Error{HHG_ENOCONV, "coarse solve did not reach its tolerance"};
@@ -540,7 +709,7 @@ static void vcycle_rec(hhg_shell* s, int n, int op, const double* f, double* u, 
     TimedScope tr(s, -1, HHG_T_TRANSFER, st);
     launch_restrict(vf, vc, C.d_coarse_low_fine, (const double*)L.d_r, C.d_f, st);
   }
-  HHG_CUDA(cudaMemsetAsync(C.d_u, 0, sizeof(double) * C.lay.n_total, st));
+  HHG_CUDA(cudaMemsetAsync(C.d_u, 0, sizeof(double) * C.lay.n_total * s->nb, st));
   vcycle_rec(s, n - 1, op, C.d_f, C.d_u, nu1, nu2, st);
   {
     TimedScope tr(s, -1, HHG_T_TRANSFER, st);
@@ -556,9 +725,9 @@ static void vcycle_rec(hhg_shell* s, int n, int op, const double* f, double* u, 
 static void vcycle_rec32(hhg_shell* s, int n, int op, const float* f, float* u, int nu1, int nu2, cudaStream_t st) {
   if (n == 0) {
     Level& C = s->levels[0];
-    launch_widen(f, C.d_f, C.lay.n_total, false, st);
+    launch_widen(f, C.d_f, C.lay.n_total * s->nb, false, st);
     coarse_solve(s, C.d_f, C.d_u, st);
-    launch_copy_cast<float>(C.d_u, u, C.lay.n_total, st);
+    launch_copy_cast<float>(C.d_u, u, C.lay.n_total * s->nb, st);
     return;
   }
   Level& L = s->levels[n];
@@ -570,7 +739,7 @@ static void vcycle_rec32(hhg_shell* s, int n, int op, const float* f, float* u, 
     TimedScope tr(s, -1, HHG_T_TRANSFER, st);
     launch_restrict(vf, vc, C.d_coarse_low_fine, (const float*)L.d_r32, C.d_f32, st);
   }
-  HHG_CUDA(cudaMemsetAsync(C.d_u32, 0, sizeof(float) * C.lay.n_total, st));
+  HHG_CUDA(cudaMemsetAsync(C.d_u32, 0, sizeof(float) * C.lay.n_total * s->nb, st));
   vcycle_rec32(s, n - 1, op, C.d_f32, C.d_u32, nu1, nu2, st);
   {
     TimedScope tr(s, -1, HHG_T_TRANSFER, st);
@@ -655,6 +824,9 @@ static void fit(hhg_shell* s, int q, int j, cudaStream_t st) {
   }
   s->q = q;
   s->j = j;
+  ++s->gen;
+  s->cg_graph_iters = 0;
+  tune_smooth32(s, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -746,6 +918,7 @@ hhg_status hhg_timing(hhg_shell* s, int enable) {
   return guarded([&] {
     HHG_CHECK(s != nullptr, HHG_EINVAL, "NULL shell");
     if (!enable) timing_clear(s);
+    if (s->timing != (enable != 0)) ++s->gen;  // a captured cycle holds (or lacks) the timers' events
     s->timing = enable != 0;
   });
 }
@@ -761,8 +934,10 @@ hhg_status hhg_timing_read(hhg_shell* s, int which, double* total_ms, int64_t* l
       HHG_CUDA(cudaEventElapsedTime(&ms, p.first, p.second));
       tot += ms;
     }
+    tot += s->gsum[which];
     if (total_ms) *total_ms = tot;
-    if (launches) *launches = which == HHG_T_COARSE ? s->cg_iters : (int64_t)s->tevents[which].size();
+    if (launches)
+      *launches = which == HHG_T_COARSE ? s->cg_iters : (int64_t)s->tevents[which].size() + s->gcnt[which];
   });
 }
 
@@ -793,21 +968,25 @@ hhg_status hhg_setup_shell(const hhg_shell_desc* d, void* stream, hhg_shell** ou
           geom[c].r[a] = s->mesh.vr[v];
         }
       s->d_geom = upload(s->alloc, geom, st);
+      HHG_CUDA(cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking));
+      for (cudaEvent_t& e : s->gev) HHG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
       s->d_err = s->alloc.alloc_n<int>(4);
       HHG_CUDA(cudaMemsetAsync(s->d_err, 0, 4 * sizeof(int), st));
       s->levels.resize(s->Lf - 1);
       for (int n = 0; n < (int)s->levels.size(); ++n) build_level(s, n, st);
       // reduction scratch: 64 scalar slots, then partial sums (per-cell and
       // per-block residual partials, or the coarse solver's 3 CG_BLOCKS)
-      int64_t red = 64 + 3 * CG_BLOCKS;
-      for (auto& L : s->levels) red = std::max<int64_t>(red, 64 + L.lay.nC + low_blocks(L.lay.off_C));
-      s->red_len = red + 64;
+      int64_t ps = 3 * CG_BLOCKS;
+      for (auto& L : s->levels) ps = std::max<int64_t>(ps, L.lay.nC + low_blocks(L.lay.off_C));
+      s->pstride = (int)ps;
+      s->red_len = 64 + ps;
       s->d_red = s->alloc.alloc_n<double>((size_t)s->red_len);
       HHG_CUDA(cudaMemsetAsync(s->d_red, 0, sizeof(double) * s->red_len, st));
       {
         const Level& L0 = s->levels[0];
         const int64_t n0 = L0.lay.n_total;
-        s->d_cg = s->alloc.alloc_n<double>((size_t)(5 * n0));
+        s->d_cg = s->alloc.alloc_n<double>((size_t)(4 * n0));
+        double* dinv = s->alloc.alloc_n<double>((size_t)n0);
         CoarseOp* A = new CoarseOp{};
         s->coarse_op = A;
         A->n_total = n0;
@@ -820,10 +999,13 @@ hhg_status hhg_setup_shell(const hhg_shell_desc* d, void* stream, hhg_shell** ou
         int* col = s->alloc.alloc_n<int>((size_t)(14 * L0.lay.nC));
         double* val = s->alloc.alloc_n<double>((size_t)(14 * L0.lay.nC));
         double* diag = s->alloc.alloc_n<double>((size_t)L0.lay.nC);
-        launch_coarse_setup(view<double>(s, 0), *A, col, val, diag, s->d_cg + 4 * n0, st);
+        launch_coarse_setup(view<double>(s, 0), *A, col, val, diag, dinv, st);
       }
       HHG_CUDA(cudaStreamSynchronize(st));
     } catch (...) {
+      if (s->gstream) cudaStreamDestroy(s->gstream);
+      for (cudaEvent_t e : s->gev)
+        if (e) cudaEventDestroy(e);
       s->alloc.release_all();
       delete static_cast<CoarseOp*>(s->coarse_op);
       delete s;
@@ -838,9 +1020,40 @@ hhg_status hhg_destroy(hhg_shell* s) {
     if (!s) return;
     cudaDeviceSynchronize();
     timing_clear(s);
+    if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
+    graph_timed_clear(s);
+    if (s->gstream) cudaStreamDestroy(s->gstream);
+    for (cudaEvent_t e : s->gev)
+      if (e) cudaEventDestroy(e);
     delete static_cast<CoarseOp*>(s->coarse_op);
     s->alloc.release_all();
     delete s;
+  });
+}
+
+hhg_status hhg_tuning(const hhg_shell* s, int L, int* cfg, double* ms) {
+  return guarded([&] {
+    const int n = level_index(const_cast<hhg_shell*>(s), L);
+    const Level& Lv = s->levels[n];
+    if (cfg) *cfg = Lv.tune32;
+    if (ms)
+      for (int t = 0; t <= STAGE32_CONFIGS; ++t) ms[t] = Lv.tune32 == -2 ? -1.0 : Lv.tune32_ms[t];
+  });
+}
+
+hhg_status hhg_set_graphs(hhg_shell* s, int enable) {
+  return guarded([&] {
+    HHG_CHECK(s != nullptr, HHG_EINVAL, "NULL shell");
+    s->graphs = enable != 0;
+  });
+}
+
+hhg_status hhg_set_tuning(hhg_shell* s, int L, int cfg) {
+  return guarded([&] {
+    const int n = level_index(s, L);
+    HHG_CHECK(cfg >= -1 && cfg < STAGE32_CONFIGS, HHG_EINVAL, "unknown smoother configuration");
+    s->levels[n].tune32 = cfg;
+    ++s->gen;
   });
 }
 
@@ -875,6 +1088,69 @@ static void check_common(hhg_shell* s, int n, int op, int dtype, int nrhs) {
   check_op(s, n, op);
 }
 
+// Grows every per-right-hand-side buffer of the shell (halo copies, work
+// vectors, step buffers, reduction and coarse-solver scratch) to hold nrhs
+// vectors.  Contents are not kept: every operation initialises what it reads.
+static void ensure_cap(hhg_shell* s, int nrhs, cudaStream_t st) {
+  if (nrhs <= s->cap) return;
+  HHG_CUDA(cudaStreamSynchronize(st));
+  Allocator& A = s->alloc;
+  const int64_t cap = nrhs;
+  auto regrow = [&](auto*& p, int64_t per) {
+    using E = std::remove_reference_t<decltype(*p)>;
+    if (!p) return;
+    A.release(p);
+    p = nullptr;
+    p = A.alloc_n<E>((size_t)(cap * std::max<int64_t>(per, 1)));
+    HHG_CUDA(cudaMemsetAsync(p, 0, sizeof(E) * cap * std::max<int64_t>(per, 1), st));
+  };
+  for (auto& L : s->levels) {
+    const int64_t nt = L.lay.n_total, ng = L.lay.nC * L.lay.n_full, ntmp = std::max(L.max_step, 1);
+    regrow(L.d_ghost64, ng);
+    regrow(L.d_r, nt);
+    regrow(L.d_tmp, ntmp);
+    regrow(L.d_u, nt);
+    regrow(L.d_f, nt);
+    regrow(L.d_ghost32, ng);
+    regrow(L.d_u32, nt);
+    regrow(L.d_f32, nt);
+    regrow(L.d_r32, nt);
+    regrow(L.d_tmp32, ntmp);
+  }
+  A.release(s->d_red);
+  s->d_red = nullptr;
+  s->red_len = (64 + (int64_t)s->pstride) * cap;
+  s->d_red = A.alloc_n<double>((size_t)s->red_len);
+  HHG_CUDA(cudaMemsetAsync(s->d_red, 0, sizeof(double) * s->red_len, st));
+  A.release(s->d_cg);
+  s->d_cg = nullptr;
+  s->d_cg = A.alloc_n<double>((size_t)(4 * s->levels[0].lay.n_total * cap));
+  HHG_CUDA(cudaStreamSynchronize(st));
+  s->cap = (int)cap;
+  ++s->gen;
+}
+
+// Sets the number of right-hand sides the next operations process together
+// and restores one on scope exit.
+struct Batch {
+  hhg_shell* s;
+  Batch(hhg_shell* s_, int nb, cudaStream_t st) : s(s_) {
+    ensure_cap(s, nb, st);
+    s->nb = nb;
+  }
+  ~Batch() { s->nb = 1; }
+};
+
+// All vector arguments in device memory: the batched path (every kernel
+// takes all right-hand sides, the surrogate weights of a node are evaluated
+// once for all of them); otherwise one right-hand side at a time through the
+// staging buffers.
+static bool all_device(std::initializer_list<const void*> ps) {
+  for (const void* p : ps)
+    if (p == nullptr || is_host_ptr(p)) return false;
+  return true;
+}
+
 hhg_status hhg_apply(hhg_shell* s, int L, hhg_op op, hhg_dtype dtype, const void* u, void* y, int nrhs,
                      void* stream) {
   return guarded([&] {
@@ -884,6 +1160,12 @@ hhg_status hhg_apply(hhg_shell* s, int L, hhg_op op, hhg_dtype dtype, const void
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t nt = s->levels[n].lay.n_total;
     if (dtype == HHG_F32) ensure_f32(s, st);
+    if (nrhs > 1 && all_device({u, y})) {
+      Batch bt(s, nrhs, st);
+      if (dtype == HHG_F32) op_apply<float>(s, n, op, (const float*)u, (float*)y, st);
+      else op_apply(s, n, op, (const double*)u, (double*)y, st);
+      return;
+    }
     for (int b = 0; b < nrhs; ++b) {
       if (dtype == HHG_F32) {
         Arg au = stage_in(s, 0, (const float*)u + b * nt, nt, true, st, sizeof(float));
@@ -908,6 +1190,16 @@ hhg_status hhg_residual(hhg_shell* s, int L, hhg_op op, hhg_dtype dtype, const v
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t nt = s->levels[n].lay.n_total;
     if (dtype == HHG_F32) ensure_f32(s, st);
+    if (nrhs > 1 && all_device({u, f, r})) {
+      Batch bt(s, nrhs, st);
+      if (dtype == HHG_F32) op_residual<float>(s, n, op, (const float*)u, (const float*)f, (float*)r, 9, st);
+      else op_residual(s, n, op, (const double*)u, (const double*)f, (double*)r, 9, st);
+      if (norms) {
+        const std::vector<double> h = read_scalars(s, 9, st);
+        for (int b = 0; b < nrhs; ++b) norms[b] = std::sqrt(h[b]);
+      }
+      return;
+    }
     for (int b = 0; b < nrhs; ++b) {
       if (dtype == HHG_F32) {
         Arg au = stage_in(s, 0, (const float*)u + b * nt, nt, true, st, sizeof(float));
@@ -922,7 +1214,7 @@ hhg_status hhg_residual(hhg_shell* s, int L, hhg_op op, hhg_dtype dtype, const v
         op_residual(s, n, op, au.dev, af.dev, ar.dev, 9, st);
         stage_out(ar, nt, st);
       }
-      if (norms) norms[b] = std::sqrt(read_scalar(s, 9, st));
+      if (norms) norms[b] = std::sqrt(read_scalars(s, 9, st)[0]);
     }
   });
 }
@@ -937,11 +1229,22 @@ hhg_status hhg_smooth(hhg_shell* s, int L, hhg_op op, hhg_dtype dtype, const voi
     Level& Lv = s->levels[n];
     const int64_t nt = Lv.lay.n_total;
     if (dtype == HHG_F32) ensure_f32(s, st);
+    if (nrhs > 1 && all_device({f, u})) {
+      Batch bt(s, nrhs, st);
+      if (dtype == HHG_F32) {
+        launch_zero_list(Lv.d_dirichlet, Lv.n_dirichlet, (float*)u, nrhs, nt, st);
+        for (int t = 0; t < sweeps; ++t) op_smooth<float>(s, n, op, (const float*)f, (float*)u, st);
+      } else {
+        launch_zero_list(Lv.d_dirichlet, Lv.n_dirichlet, (double*)u, nrhs, nt, st);
+        for (int t = 0; t < sweeps; ++t) op_smooth(s, n, op, (const double*)f, (double*)u, st);
+      }
+      return;
+    }
     for (int b = 0; b < nrhs; ++b) {
       if (dtype == HHG_F32) {
         Arg af = stage_in(s, 1, (const float*)f + b * nt, nt, true, st, sizeof(float));
         Arg au = stage_in(s, 0, (float*)u + b * nt, nt, true, st, sizeof(float));
-        launch_zero_list(Lv.d_dirichlet, Lv.n_dirichlet, au.dev32(), st);
+        launch_zero_list(Lv.d_dirichlet, Lv.n_dirichlet, au.dev32(), 1, nt, st);
         for (int t = 0; t < sweeps; ++t) op_smooth<float>(s, n, op, af.dev32(), au.dev32(), st);
         stage_out(au, nt, st);
         if (au.host) check_device_error(s, st);
@@ -949,11 +1252,107 @@ hhg_status hhg_smooth(hhg_shell* s, int L, hhg_op op, hhg_dtype dtype, const voi
       }
       Arg af = stage_in(s, 1, (const double*)f + b * nt, nt, true, st);
       Arg au = stage_in(s, 0, (double*)u + b * nt, nt, true, st);
-      launch_zero_list(Lv.d_dirichlet, Lv.n_dirichlet, au.dev, st);
+      launch_zero_list(Lv.d_dirichlet, Lv.n_dirichlet, au.dev, 1, nt, st);
       for (int t = 0; t < sweeps; ++t) op_smooth(s, n, op, af.dev, au.dev, st);
       stage_out(au, nt, st);
     }
   });
+}
+
+// V-cycles for the active right-hand sides (s->nb of them, device vectors f
+// and u, nt apart) until every relative residual is <= rtol or max_cycles;
+// rel receives the final relative residuals, the return value is the number
+// of cycles run.
+static int solve_batch(hhg_shell* s, int op, int dtype, const double* f, double* u, int nu1, int nu2, int max_cycles,
+                       double rtol, double* rel, cudaStream_t st) {
+  const int n = (int)s->levels.size() - 1, nb = s->nb;
+  Level& Lv = s->levels[n];
+  const int64_t nt = Lv.lay.n_total;
+  launch_zero_list(Lv.d_dirichlet, Lv.n_dirichlet, u, nb, nt, st);
+  op_residual(s, n, op, u, f, Lv.d_r, 10, st);
+  std::vector<double> r0 = read_scalars(s, 10, st);
+  bool todo = false;
+  for (int b = 0; b < nb; ++b) {
+    r0[b] = std::sqrt(r0[b]);
+    HHG_CHECK(std::isfinite(r0[b]), HHG_EDIVERGED, "initial residual is not finite");
+    rel[b] = r0[b] > 0 ? 1.0 : 0.0;
+    todo = todo || rel[b] > rtol;
+  }
+  if (dtype == HHG_F32) ensure_f32(s, st);
+  auto cycle = [&](cudaStream_t cs) {
+    if (dtype == HHG_F32) {
+      // iterative refinement: e = one FP32 V-cycle on L e = r (e0 = 0), u += e
+      launch_copy_cast<float>(Lv.d_r, Lv.d_f32, nt * nb, cs);
+      HHG_CUDA(cudaMemsetAsync(Lv.d_u32, 0, sizeof(float) * nt * nb, cs));
+      vcycle_rec32(s, n, op, Lv.d_f32, Lv.d_u32, nu1, nu2, cs);
+      launch_widen(Lv.d_u32, u, nt * nb, true, cs);
+    } else {
+      vcycle_rec(s, n, op, f, u, nu1, nu2, cs);
+    }
+  };
+  // The first cycle runs launch by launch (its coarse solve is host-driven
+  // and sets the iteration count); later cycles replay one CUDA graph of the
+  // whole cycle, captured once per key, with fixed-count coarse iterations.
+  // Graphs are captured and launched on the shell's own stream, ordered
+  // after and before the caller's stream by events.
+  const bool graphs = s->graphs;
+  int cyc = 0;
+  while (todo && cyc < max_cycles) {
+    if (!graphs || cyc == 0) {
+      cycle(st);
+      if (cyc == 0 && s->cg_graph_iters == 0) s->cg_graph_iters = std::max(32, (s->cg_last * 3 / 2 + 16 + 7) / 8 * 8);
+    } else {
+      const hhg_shell::GraphKey key{f, u, nb, op, dtype, nu1, nu2, s->cg_graph_iters, s->gen};
+      if (!s->graph_exec || !(s->graph_key == key)) {
+        if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
+        s->graph_exec = nullptr;
+        cudaGraph_t g = nullptr;
+        graph_timed_clear(s);
+        HHG_CUDA(cudaStreamBeginCapture(s->gstream, cudaStreamCaptureModeRelaxed));
+        s->cg_fixed = s->cg_graph_iters;
+        s->capturing = true;
+        const int64_t l0 = hhg_launch_count();
+        try {
+          cycle(s->gstream);
+        } catch (...) {
+          s->cg_fixed = 0;
+          s->capturing = false;
+          cudaStreamEndCapture(s->gstream, &g);
+          if (g) cudaGraphDestroy(g);
+          throw;
+        }
+        s->graph_launches = hhg_launch_count() - l0;
+        count_launch((int)-s->graph_launches);  // counted per replay instead
+        s->cg_fixed = 0;
+        s->capturing = false;
+        HHG_CUDA(cudaStreamEndCapture(s->gstream, &g));
+        const cudaError_t ie = cudaGraphInstantiate(&s->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        HHG_CUDA(ie);
+        s->graph_key = key;
+      }
+      HHG_CUDA(cudaEventRecord(s->gev[0], st));
+      HHG_CUDA(cudaStreamWaitEvent(s->gstream, s->gev[0], 0));
+      HHG_CUDA(cudaGraphLaunch(s->graph_exec, s->gstream));
+      count_launch((int)s->graph_launches);
+      HHG_CUDA(cudaEventRecord(s->gev[1], s->gstream));
+      HHG_CUDA(cudaStreamWaitEvent(st, s->gev[1], 0));
+    }
+    op_residual(s, n, op, u, f, Lv.d_r, 10, st);
+    const std::vector<double> rn = read_scalars(s, 10, st);
+    if (graphs && cyc > 0) graph_timed_accumulate(s);
+    check_device_error(s, st);
+    todo = false;
+    for (int b = 0; b < nb; ++b) {
+      const double v = std::sqrt(rn[b]);
+      HHG_CHECK(std::isfinite(v), HHG_EDIVERGED, "residual norm became NaN or Inf");
+      rel[b] = r0[b] > 0 ? v / r0[b] : 0.0;
+      todo = todo || rel[b] > rtol;
+    }
+    ++cyc;
+  }
+  launch_zero_list(Lv.d_dirichlet, Lv.n_dirichlet, u, nb, nt, st);
+  return cyc;
 }
 
 hhg_status hhg_vcycle(hhg_shell* s, hhg_op op, hhg_dtype dtype, const void* f, void* u, int nu1, int nu2,
@@ -967,42 +1366,26 @@ hhg_status hhg_vcycle(hhg_shell* s, hhg_op op, hhg_dtype dtype, const void* f, v
     cudaStream_t st = (cudaStream_t)stream;
     Level& Lv = s->levels[n];
     const int64_t nt = Lv.lay.n_total;
+    std::vector<double> rel((size_t)nrhs, 0.0);
     int cycles_max = 0;
-    bool all_conv = true;
-    for (int b = 0; b < nrhs; ++b) {
-      Arg af = stage_in(s, 1, (const double*)f + b * nt, nt, true, st);
-      Arg au = stage_in(s, 0, (double*)u + b * nt, nt, true, st);
-      launch_zero_list(Lv.d_dirichlet, Lv.n_dirichlet, au.dev, st);
-      op_residual(s, n, op, au.dev, af.dev, Lv.d_r, 10, st);
-      const double r0 = std::sqrt(read_scalar(s, 10, st));
-      HHG_CHECK(std::isfinite(r0), HHG_EDIVERGED, "initial residual is not finite");
-      double rel = r0 > 0 ? 1.0 : 0.0;
-      int cyc = 0;
-      if (dtype == HHG_F32) ensure_f32(s, st);
-      while (rel > rtol && cyc < max_cycles) {
-        if (dtype == HHG_F32) {
-          // iterative refinement: e = one FP32 V-cycle on L e = r (e0 = 0), u += e
-          launch_copy_cast<float>(Lv.d_r, Lv.d_f32, nt, st);
-          HHG_CUDA(cudaMemsetAsync(Lv.d_u32, 0, sizeof(float) * nt, st));
-          vcycle_rec32(s, n, op, Lv.d_f32, Lv.d_u32, nu1, nu2, st);
-          launch_widen(Lv.d_u32, au.dev, nt, true, st);
-        } else {
-          vcycle_rec(s, n, op, af.dev, au.dev, nu1, nu2, st);
-        }
-        op_residual(s, n, op, au.dev, af.dev, Lv.d_r, 10, st);
-        const double rn = std::sqrt(read_scalar(s, 10, st));
-        check_device_error(s, st);
-        HHG_CHECK(std::isfinite(rn), HHG_EDIVERGED, "residual norm became NaN or Inf");
-        rel = rn / r0;
-        ++cyc;
+    if (nrhs > 1 && all_device({f, u})) {
+      Batch bt(s, nrhs, st);
+      cycles_max = solve_batch(s, op, dtype, (const double*)f, (double*)u, nu1, nu2, max_cycles, rtol, rel.data(), st);
+    } else {
+      for (int b = 0; b < nrhs; ++b) {
+        Arg af = stage_in(s, 1, (const double*)f + b * nt, nt, true, st);
+        Arg au = stage_in(s, 0, (double*)u + b * nt, nt, true, st);
+        const int cyc = solve_batch(s, op, dtype, af.dev, au.dev, nu1, nu2, max_cycles, rtol, &rel[b], st);
+        stage_out(au, nt, st);
+        cycles_max = std::max(cycles_max, cyc);
       }
-      launch_zero_list(Lv.d_dirichlet, Lv.n_dirichlet, au.dev, st);
-      stage_out(au, nt, st);
-      if (relres_out) relres_out[b] = rel;
-      cycles_max = std::max(cycles_max, cyc);
-      if (rel > rtol) all_conv = false;
     }
     HHG_CUDA(cudaStreamSynchronize(st));
+    bool all_conv = true;
+    for (int b = 0; b < nrhs; ++b) {
+      if (relres_out) relres_out[b] = rel[b];
+      all_conv = all_conv && rel[b] <= rtol;
+    }
     if (cycles_out) *cycles_out = cycles_max;
     if (!all_conv) throw Error{HHG_ENOCONV, "max_cycles reached before rtol"};
   });
@@ -1050,6 +1433,7 @@ extern "C" hhg_status hhg_residual_noalloc(hhg_shell* s, int L, hhg_op op, const
     for (const void* p : {(const void*)u, (const void*)f, (const void*)r, (const void*)norm2_dev})
       HHG_CHECK(!is_host_ptr(p), HHG_EINVAL, "hhg_residual_noalloc takes device pointers only");
     LevelView<double> v = view<double>(s, n);
+    v.nrhs = 1;
     const int nb = low_blocks(v.off_C);
     HHG_CHECK((int64_t)v.nC + nb <= HHG_NOALLOC_SCRATCH, HHG_EINVAL,
               "level needs " + std::to_string((int64_t)v.nC + nb) + " partial slots, more than HHG_NOALLOC_SCRATCH (" +
@@ -1059,6 +1443,6 @@ extern "C" hhg_status hhg_residual_noalloc(hhg_shell* s, int L, hhg_op op, const
     launch_halo(v, u, st);
     launch_cell(v, eff_op(s, n, op), RESIDUAL, const_cast<double*>(u), r, f, part, st);
     launch_low(v, RESIDUAL, u, r, f, part + v.nC, nb, st);
-    launch_sum(part, v.nC + nb, norm2_dev, st);
+    launch_sum(part, v.nC + nb, 1, 0, norm2_dev, st);
   });
 }

@@ -28,6 +28,8 @@
 // closed-form 32-bit offsets within the cell's block of the canonical
 // vector; nodes next to the cell boundary read boundary neighbours from the
 // cell's halo copy.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -38,9 +40,6 @@ namespace hhg {
 namespace {
 
 constexpr int NODE_THREADS = 256;  // thread-per-node kernels
-// FP32 smoother: shared-memory staged one-launch sweep (stage.cu) instead of
-// four colour launches of the thread-per-node kernel.
-constexpr bool kStagedSmoother = false;
 
 // Coefficients of the polynomial in i along line (j, k): c_a(j, k) =
 // sum_{b,d} A_{a,b,d} j^b k^d.  Storage order of A (per direction):
@@ -120,6 +119,19 @@ __device__ __forceinline__ void node_update(const LevelView<T>& lv, int c, int i
     body([&](int w) -> T { return load_pt(lv, (const T*)u, c, i + DI(w), j + DJ(w), k + DK(w)); });
   }
 }
+
+// Right-hand sides per batched launch: the weights of a node are evaluated
+// once and applied to RB vectors.
+constexpr int RB = 4;
+
+// The update of node (i, j, k) of cell c for right-hand sides b0 .. b0+G-1
+// (G <= RB) with its 15 weights w[] already evaluated.  CHAIN: one FMA chain
+// in direction order and the Newton-Raphson divide (the FP64 surrogate
+// kernel's arithmetic); otherwise node_update's two-accumulator form.
+template <class T, Mode MODE, bool CHAIN, class W>
+__device__ __forceinline__ void node_update_batch(const LevelView<T>& lv, int c, int i, int j, int k, const W* w,
+                                                  T* u, T* out, const T* f, double (&nrm)[RB], int b0, int G,
+                                                  T scale, T inv_scale);
 
 // ---------------------------------------------------------------------------
 // FP64 surrogate: line table at fit time, thread-per-node application
@@ -281,6 +293,104 @@ __device__ __forceinline__ void lsqp64_node(const long long* __restrict__ C, uns
   }
 }
 
+template <class T, Mode MODE, bool CHAIN, class W>
+__device__ __forceinline__ void node_update_batch(const LevelView<T>& lv, int c, int i, int j, int k, const W* w,
+                                                  T* u, T* out, const T* f, double (&nrm)[RB], int b0, int G,
+                                                  T scale, T inv_scale) {
+  const int64_t I = lv.off_C + (int64_t)c * lv.n_int + lin_interior32(i, j, k, lv.N);
+  const bool deep = deep_interior(i, j, k, lv.N);
+  int off[14];
+  if (deep) neighbour_offsets(j, k, lv.N, off);
+#pragma unroll
+  for (int g = 0; g < RB; ++g) {
+    if (g >= G) break;
+    const int64_t b = b0 + g;
+    T* ub = u + b * lv.vstride;
+    const T* gb = lv.ghost + b * lv.gstride;
+    auto nb = [&](int v) -> T {
+      if (deep) return ub[I + off[v]];
+      const int i2 = i + DI(v), j2 = j + DJ(v), k2 = k + DK(v);
+      if (is_interior(i2, j2, k2, lv.N)) return ub[lv.off_C + (int64_t)c * lv.n_int + lin_interior32(i2, j2, k2, lv.N)];
+      return gb[(int64_t)c * lv.n_full + lin_full(i2, j2, k2, lv.N)];
+    };
+    if (MODE == SMOOTH) {
+      const T fb = f[b * lv.vstride + I];
+      if (CHAIN) {
+        T acc = fb * scale;
+#pragma unroll
+        for (int v = 0; v < 14; ++v) acc = fma(-(T)w[v], nb(v), acc);
+        ub[I] = (T)div_nr((double)acc, (double)w[MC]);
+      } else {
+        T a0 = fb * scale, a1 = 0;
+#pragma unroll
+        for (int v = 0; v < 14; v += 2) {
+          a0 = fma(-(T)w[v], nb(v), a0);
+          a1 = fma(-(T)w[v + 1], nb(v + 1), a1);
+        }
+        ub[I] = (a0 + a1) / (T)w[MC];
+      }
+    } else {
+      T y;
+      if (CHAIN) {
+        y = (T)w[MC] * ub[I];
+#pragma unroll
+        for (int v = 0; v < 14; ++v) y = fma((T)w[v], nb(v), y);
+      } else {
+        T a0 = (T)w[MC] * ub[I], a1 = 0;
+#pragma unroll
+        for (int v = 0; v < 14; v += 2) {
+          a0 = fma((T)w[v], nb(v), a0);
+          a1 = fma((T)w[v + 1], nb(v + 1), a1);
+        }
+        y = a0 + a1;
+      }
+      if (MODE == APPLY) {
+        out[b * lv.vstride + I] = y * inv_scale;
+      } else {
+        const T r = fma(-inv_scale, y, f[b * lv.vstride + I]);
+        out[b * lv.vstride + I] = r;
+        nrm[g] = CHAIN ? fma((double)r, (double)r, nrm[g]) : nrm[g] + (double)r * (double)r;
+      }
+    }
+  }
+}
+
+// Per-right-hand-side block sums of a batched residual into partial.
+__device__ __forceinline__ void batch_partials(const double (&nrm)[RB], int b0, int G, int pstride, int c,
+                                               double* partial) {
+#pragma unroll
+  for (int g = 0; g < RB; ++g) {
+    if (g >= G) break;
+    const double tot = block_sum(nrm[g]);
+    if (threadIdx.x == 0) partial[(int64_t)(b0 + g) * pstride + c] = tot;
+  }
+}
+
+// FP64 surrogate for RB right-hand sides at once: the 15 weights of a node
+// are formed once (integer pipe) and applied to every vector of the group.
+template <int Q, Mode MODE>
+__global__ void __launch_bounds__(NODE_THREADS, 2) lsqp_node_batch_kernel(LevelView<double> lv,
+                                                                          const uint32_t* __restrict__ list, int n_list,
+                                                                          double* u, double* out, const double* f,
+                                                                          double* partial, int b0, int G) {
+  const int c = blockIdx.x;
+  const int N = lv.N;
+  const int E = lv.cell_e[c];
+  const double scale = ldexp(1.0, E), inv_scale = ldexp(1.0, -E);
+  const long long* tab = lv.line64 + (int64_t)c * lv.n_lines * line_rec(Q);
+  double nrm[RB] = {};
+  for (int t = threadIdx.x; t < n_list; t += blockDim.x) {
+    const uint32_t p = list[t];
+    const int i = unpack_i(p), j = unpack_j(p), k = unpack_k(p);
+    const long long* C = tab + (int64_t)line_id(j, k, N) * line_rec(Q);
+    double w[15];
+#pragma unroll
+    for (int v = 0; v < 15; ++v) w[v] = i64_to_f64(horner_i64<Q>(C + v * (Q + 1), (unsigned)i));
+    node_update_batch<double, MODE, true>(lv, c, i, j, k, w, u, out, f, nrm, b0, G, scale, inv_scale);
+  }
+  if (MODE == RESIDUAL) batch_partials(nrm, b0, G, lv.pstride, c, partial);
+}
+
 template <int Q, Mode MODE>
 __global__ void __launch_bounds__(NODE_THREADS, 3) lsqp_node_kernel(LevelView<double> lv, const uint32_t* __restrict__ list,
                                                                   int n_list, double* u, double* out, const double* f,
@@ -380,6 +490,38 @@ __global__ void __launch_bounds__(NODE_THREADS, 4) lsqp_node32_kernel(LevelView<
   }
 }
 
+// FP32 surrogate for RB right-hand sides at once (weights evaluated once per
+// node from the per-plane table in shared memory).
+template <int Q, Mode MODE>
+__global__ void __launch_bounds__(NODE_THREADS, 2) lsqp_node32_batch_kernel(LevelView<float> lv,
+                                                                            const uint32_t* __restrict__ list,
+                                                                            int n_list, float* u, float* out,
+                                                                            const float* f, double* partial, int b0,
+                                                                            int G) {
+  constexpr int NP = (Q + 1) * (Q + 2) / 2;
+  constexpr int NPP = np_pad<Q>();
+  extern __shared__ __align__(16) float s_tab[];   // [N - 3][15][NPP]
+  const int c = blockIdx.x;
+  const int np = lv.N - 3;
+  const float* tab = lv.plane32 + (int64_t)c * np * 15 * NP;
+  for (int t = threadIdx.x; t < np * 15 * NPP; t += blockDim.x) {
+    const int e = t % NPP, pw = t / NPP;
+    s_tab[t] = e < NP ? tab[pw * NP + e] : 0.0f;
+  }
+  __syncthreads();
+  double nrm[RB] = {};
+  for (int t = threadIdx.x; t < n_list; t += blockDim.x) {
+    const uint32_t p = list[t];
+    const int i = unpack_i(p), j = unpack_j(p), k = unpack_k(p);
+    const float* P = s_tab + (k - 1) * 15 * NPP;
+    float w[15];
+#pragma unroll
+    for (int v = 0; v < 15; ++v) w[v] = eval_plane<float, Q>(P + v * NPP, (float)i, (float)j);
+    node_update_batch<float, MODE, false>(lv, c, i, j, k, w, u, out, f, nrm, b0, G, 1.0f, 1.0f);
+  }
+  if (MODE == RESIDUAL) batch_partials(nrm, b0, G, lv.pstride, c, partial);
+}
+
 // ---------------------------------------------------------------------------
 // IFEM: exact stencils assembled on the fly, thread per node
 // ---------------------------------------------------------------------------
@@ -408,6 +550,27 @@ __global__ void __launch_bounds__(NODE_THREADS) ifem_node_kernel(LevelView<T> lv
   }
 }
 
+// IFEM for RB right-hand sides at once (one stencil assembly per node).
+template <class T, Mode MODE>
+__global__ void __launch_bounds__(NODE_THREADS) ifem_node_batch_kernel(LevelView<T> lv, const uint32_t* __restrict__ list,
+                                                                        int n_list, T* u, T* out, const T* f,
+                                                                        double* partial, int b0, int G) {
+  __shared__ CellGeom g;
+  const int c = blockIdx.x;
+  if (threadIdx.x < 16)
+    reinterpret_cast<double*>(&g)[threadIdx.x] = reinterpret_cast<const double*>(&lv.geom[c])[threadIdx.x];
+  __syncthreads();
+  double nrm[RB] = {};
+  for (int t = threadIdx.x; t < n_list; t += blockDim.x) {
+    const uint32_t p = list[t];
+    const int i = unpack_i(p), j = unpack_j(p), k = unpack_k(p);
+    double s[15];
+    ifem_stencil(g, lv.N, i, j, k, s);
+    node_update_batch<T, MODE, false>(lv, c, i, j, k, s, u, out, f, nrm, b0, G, T(1), T(1));
+  }
+  if (MODE == RESIDUAL) batch_partials(nrm, b0, G, lv.pstride, c, partial);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -416,9 +579,18 @@ template <int Q, Mode MODE>
 void launch_node64(const LevelView<double>& lv, const uint32_t* list, int n, double* u, double* out, const double* f,
                    double* partial, cudaStream_t st) {
   HHG_CHECK(lv.line64 != nullptr, HHG_ENOTFIT, "FP64 surrogate line table missing");
-  lsqp_node_kernel<Q, MODE><<<lv.nC, NODE_THREADS, 0, st>>>(lv, list, n, u, out, f, partial);
-  HHG_CUDA(cudaGetLastError());
-  count_launch();
+  if (lv.nrhs == 1) {
+    lsqp_node_kernel<Q, MODE><<<lv.nC, NODE_THREADS, 0, st>>>(lv, list, n, u, out, f, partial);
+    HHG_CUDA(cudaGetLastError());
+    count_launch();
+    return;
+  }
+  for (int b0 = 0; b0 < lv.nrhs; b0 += RB) {
+    lsqp_node_batch_kernel<Q, MODE><<<lv.nC, NODE_THREADS, 0, st>>>(lv, list, n, u, out, f, partial, b0,
+                                                                    std::min(RB, lv.nrhs - b0));
+    HHG_CUDA(cudaGetLastError());
+    count_launch();
+  }
 }
 
 template <int Q>
@@ -440,11 +612,21 @@ void launch_node32(const LevelView<float>& lv, const uint32_t* list, int n, floa
                    double* partial, cudaStream_t st) {
   HHG_CHECK(lv.plane32 != nullptr, HHG_ENOTFIT, "FP32 surrogate plane table missing");
   const size_t smem = sizeof(float) * (size_t)(lv.N - 3) * 15 * np_pad<Q>();
-  auto kern = lsqp_node32_kernel<Q, MODE>;
-  if (smem > 48 * 1024) HHG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<lv.nC, NODE_THREADS, smem, st>>>(lv, list, n, u, out, f, partial);
-  HHG_CUDA(cudaGetLastError());
-  count_launch();
+  if (lv.nrhs == 1) {
+    auto kern = lsqp_node32_kernel<Q, MODE>;
+    ensure_smem_limit((const void*)kern, smem);
+    kern<<<lv.nC, NODE_THREADS, smem, st>>>(lv, list, n, u, out, f, partial);
+    HHG_CUDA(cudaGetLastError());
+    count_launch();
+    return;
+  }
+  auto kern = lsqp_node32_batch_kernel<Q, MODE>;
+  ensure_smem_limit((const void*)kern, smem);
+  for (int b0 = 0; b0 < lv.nrhs; b0 += RB) {
+    kern<<<lv.nC, NODE_THREADS, smem, st>>>(lv, list, n, u, out, f, partial, b0, std::min(RB, lv.nrhs - b0));
+    HHG_CUDA(cudaGetLastError());
+    count_launch();
+  }
 }
 
 template <int Q>
@@ -464,9 +646,18 @@ void lsqp32(const LevelView<float>& lv, Mode mode, float* u, float* out, const f
 template <class T, Mode MODE>
 void launch_ifem(const LevelView<T>& lv, const uint32_t* list, int n, T* u, T* out, const T* f, double* partial,
                  cudaStream_t st) {
-  ifem_node_kernel<T, MODE><<<lv.nC, NODE_THREADS, 0, st>>>(lv, list, n, u, out, f, partial);
-  HHG_CUDA(cudaGetLastError());
-  count_launch();
+  if (lv.nrhs == 1) {
+    ifem_node_kernel<T, MODE><<<lv.nC, NODE_THREADS, 0, st>>>(lv, list, n, u, out, f, partial);
+    HHG_CUDA(cudaGetLastError());
+    count_launch();
+    return;
+  }
+  for (int b0 = 0; b0 < lv.nrhs; b0 += RB) {
+    ifem_node_batch_kernel<T, MODE><<<lv.nC, NODE_THREADS, 0, st>>>(lv, list, n, u, out, f, partial, b0,
+                                                                    std::min(RB, lv.nrhs - b0));
+    HHG_CUDA(cudaGetLastError());
+    count_launch();
+  }
 }
 
 template <class T>
@@ -549,8 +740,15 @@ void launch_cell<float>(const LevelView<float>& lv, int op, Mode mode, float* u,
                         double* partial, cudaStream_t st) {
   if (lv.N < 4 || lv.n_int == 0) return;
   if (op == HHG_OP_LSQP && lv.q > 0) {
-    if (mode == SMOOTH && kStagedSmoother && stage32_supported(lv, u)) {
-      launch_stage32_smooth(lv, u, f, st);
+    if (mode == SMOOTH && lv.smooth_cfg >= 0 && stage32_supported(lv, u, lv.smooth_cfg) &&
+        (lv.nrhs == 1 || (lv.vstride % 4) == 0)) {
+      // one launch per right-hand side (the plane ring holds one vector)
+      for (int b = 0; b < lv.nrhs; ++b) {
+        LevelView<float> one = lv;
+        one.nrhs = 1;
+        one.ghost = lv.ghost + b * lv.gstride;
+        launch_stage32_smooth(one, u + b * lv.vstride, f + b * lv.vstride, lv.smooth_cfg, st);
+      }
       return;
     }
     switch (lv.q) {

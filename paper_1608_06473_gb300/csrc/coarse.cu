@@ -9,7 +9,9 @@
 // pre-assembled lower-primitive rows.  One iteration is three kernels; each
 // kernel's blocks re-sum the previous kernel's per-block partials in a fixed
 // order, so no separate reduction launch is needed and the result is
-// deterministic.
+// deterministic.  Several right-hand sides are solved together (grid y =
+// right-hand side; vectors n_total apart, partials 3 CG_BLOCKS apart, one
+// scalar of each kind per right-hand side).
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -76,9 +78,14 @@ __global__ void coarse_dinv_kernel(CoarseOp A, double* __restrict__ dinv) {
   dinv[r] = d != 0.0 ? 1.0 / d : 0.0;
 }
 
+// Offsets of right-hand side blockIdx.y.
+#define CG_RHS(vec) vec += (int64_t)blockIdx.y * A.n_total
+#define CG_PART(ptr) ptr += (int64_t)blockIdx.y * 3 * CG_BLOCKS
+
 // x = 0, r = f (0 on Dirichlet rows), z = D^-1 r, p = z; partials of r.z, r.r
 __global__ void cg_init_kernel(CoarseOp A, const double* __restrict__ f, double* x, double* r, double* z, double* p,
                                double* part_rz, double* part_rr) {
+  CG_RHS(f); CG_RHS(x); CG_RHS(r); CG_RHS(z); CG_RHS(p); CG_PART(part_rz); CG_PART(part_rr);
   double rz = 0.0, rr = 0.0;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < A.n_total; t += (int64_t)gridDim.x * blockDim.x) {
     const double di = A.dinv[t];
@@ -97,8 +104,18 @@ __global__ void cg_init_kernel(CoarseOp A, const double* __restrict__ f, double*
   if (threadIdx.x == 0) part_rr[blockIdx.x] = rr;
 }
 
+// Fixed-count (graph-captured) iterations skip a right-hand side once its
+// residual has converged: rr_cur <= 1e-26 ff (ff = r0.r0); rr_cur == nullptr
+// disables the test (host-driven iterations).
+__device__ __forceinline__ bool cg_converged(const double* rr_cur, const double* ff) {
+  return rr_cur != nullptr && rr_cur[blockIdx.y] <= 1e-26 * ff[blockIdx.y];
+}
+
 // q = A p; partials of p.q
-__global__ void cg_spmv_kernel(CoarseOp A, const double* __restrict__ p, double* __restrict__ q, double* part_pq) {
+__global__ void cg_spmv_kernel(CoarseOp A, const double* __restrict__ p, double* __restrict__ q, double* part_pq,
+                               const double* rr_cur, const double* ff) {
+  if (cg_converged(rr_cur, ff)) return;
+  CG_RHS(p); CG_RHS(q); CG_PART(part_pq);
   double pq = 0.0;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < A.n_total; t += (int64_t)gridDim.x * blockDim.x) {
     const double qv = coarse_row(A, t, p);
@@ -112,7 +129,11 @@ __global__ void cg_spmv_kernel(CoarseOp A, const double* __restrict__ p, double*
 // alpha = rz / pq; x += alpha p; r -= alpha q; z = D^-1 r; partials of r.z, r.r
 __global__ void cg_update_kernel(CoarseOp A, double* x, double* r, double* z, const double* __restrict__ p,
                                  const double* __restrict__ q, const double* __restrict__ part_pq,
-                                 const double* __restrict__ rz_cur, double* part_rz, double* part_rr) {
+                                 const double* __restrict__ rz_cur, double* part_rz, double* part_rr,
+                                 const double* rr_cur, const double* ff) {
+  if (cg_converged(rr_cur, ff)) return;
+  CG_RHS(x); CG_RHS(r); CG_RHS(z); CG_RHS(p); CG_RHS(q); CG_PART(part_pq); CG_PART(part_rz); CG_PART(part_rr);
+  rz_cur += blockIdx.y;
   const double pq = sum_partials(part_pq);
   const double alpha = pq != 0.0 ? *rz_cur / pq : 0.0;
   double rz = 0.0, rr = 0.0;
@@ -134,7 +155,18 @@ __global__ void cg_update_kernel(CoarseOp A, double* x, double* r, double* z, co
 // beta = rz_new / rz_cur; p = z + beta p; rz_next = rz_new, rr_out = r.r
 __global__ void cg_dir_kernel(CoarseOp A, double* p, const double* __restrict__ z, const double* __restrict__ part_rz,
                               const double* __restrict__ part_rr, const double* __restrict__ rz_cur, double* rz_next,
-                              double* rr_out) {
+                              double* rr_out, const double* rr_cur, const double* ff) {
+  if (cg_converged(rr_cur, ff)) {  // carry the scalars to the next iteration's buffers
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      rz_next[blockIdx.y] = rz_cur[blockIdx.y];
+      rr_out[blockIdx.y] = rr_cur[blockIdx.y];
+    }
+    return;
+  }
+  CG_RHS(p); CG_RHS(z); CG_PART(part_rz); CG_PART(part_rr);
+  rz_cur += blockIdx.y;
+  rz_next += blockIdx.y;
+  rr_out += blockIdx.y;
   const double rz_new = sum_partials(part_rz);
   const double o = *rz_cur;
   const double beta = o != 0.0 ? rz_new / o : 0.0;
@@ -150,15 +182,27 @@ __global__ void cg_dir_kernel(CoarseOp A, double* p, const double* __restrict__ 
 }
 
 // rz_out = sum of part_rz, rr_out = sum of part_rr (after cg_init)
+// one block per right-hand side
 __global__ void cg_sums_kernel(const double* __restrict__ part_rz, const double* __restrict__ part_rr, double* rz_out,
                                double* rr_out) {
+  part_rz += (int64_t)blockIdx.x * 3 * CG_BLOCKS;
+  part_rr += (int64_t)blockIdx.x * 3 * CG_BLOCKS;
   const double a = sum_partials(part_rz);
   const double b = sum_partials(part_rr);
   if (threadIdx.x == 0) {
-    *rz_out = a;
-    *rr_out = b;
+    rz_out[blockIdx.x] = a;
+    rr_out[blockIdx.x] = b;
   }
 }
+
+// Sets *flag when some right-hand side has not converged.
+__global__ void cg_check_kernel(const double* rr, const double* ff, int nrhs, int* flag) {
+  for (int b = threadIdx.x; b < nrhs; b += blockDim.x)
+    if (!(rr[b] <= 1e-26 * ff[b])) atomicExch(flag, 1);
+}
+
+#undef CG_RHS
+#undef CG_PART
 
 }  // namespace
 
@@ -175,23 +219,33 @@ void launch_coarse_setup(const LevelView<double>& lv, CoarseOp& A, int* col, dou
 }
 
 void launch_cg_init(const CoarseOp& A, const double* f, double* x, double* r, double* z, double* p, double* part,
-                    double* rz_out, double* rr_out, cudaStream_t st) {
-  cg_init_kernel<<<CG_BLOCKS, 256, 0, st>>>(A, f, x, r, z, p, part, part + CG_BLOCKS);
-  cg_sums_kernel<<<1, 256, 0, st>>>(part, part + CG_BLOCKS, rz_out, rr_out);
+                    double* rz_out, double* rr_out, int nrhs, cudaStream_t st) {
+  cg_init_kernel<<<dim3(CG_BLOCKS, nrhs), 256, 0, st>>>(A, f, x, r, z, p, part, part + CG_BLOCKS);
+  cg_sums_kernel<<<nrhs, 256, 0, st>>>(part, part + CG_BLOCKS, rz_out, rr_out);
   HHG_CUDA(cudaGetLastError());
   count_launch(2);
 }
 
 void launch_cg_iteration(const CoarseOp& A, double* x, double* r, double* z, double* p, double* q, double* part,
-                         const double* rz_cur, double* rz_next, double* rr_out, cudaStream_t st) {
+                         const double* rz_cur, double* rz_next, double* rr_out, int nrhs, cudaStream_t st,
+                         const double* rr_cur, const double* ff) {
   double* part_pq = part;
   double* part_rz = part + CG_BLOCKS;
   double* part_rr = part + 2 * CG_BLOCKS;
-  cg_spmv_kernel<<<CG_BLOCKS, 256, 0, st>>>(A, p, q, part_pq);
-  cg_update_kernel<<<CG_BLOCKS, 256, 0, st>>>(A, x, r, z, p, q, part_pq, rz_cur, part_rz, part_rr);
-  cg_dir_kernel<<<CG_BLOCKS, 256, 0, st>>>(A, p, z, part_rz, part_rr, rz_cur, rz_next, rr_out);
+  const dim3 g(CG_BLOCKS, nrhs);
+  cg_spmv_kernel<<<g, 256, 0, st>>>(A, p, q, part_pq, rr_cur, ff);
+  cg_update_kernel<<<g, 256, 0, st>>>(A, x, r, z, p, q, part_pq, rz_cur, part_rz, part_rr, rr_cur, ff);
+  cg_dir_kernel<<<g, 256, 0, st>>>(A, p, z, part_rz, part_rr, rz_cur, rz_next, rr_out, rr_cur, ff);
   HHG_CUDA(cudaGetLastError());
   count_launch(3);
 }
 
+}  // namespace hhg
+
+namespace hhg {
+void launch_cg_check(const double* rr, const double* ff, int nrhs, int* flag, cudaStream_t st) {
+  cg_check_kernel<<<1, 64, 0, st>>>(rr, ff, nrhs, flag);
+  HHG_CUDA(cudaGetLastError());
+  count_launch();
+}
 }  // namespace hhg

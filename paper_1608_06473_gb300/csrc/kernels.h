@@ -11,6 +11,11 @@ namespace hhg {
 
 enum Mode { APPLY = 0, RESIDUAL = 1, SMOOTH = 2 };
 
+// Raises the dynamic shared memory limit of kernel `func` to at least
+// `bytes` (never lowers it, so concurrent host threads launching the same
+// kernel with different sizes stay valid).
+void ensure_smem_limit(const void* func, size_t bytes);
+
 // ---- cell interiors (cell.cu) ----------------------------------------------
 // One CTA per macro cell (grid = nC).
 //   APPLY:    out = L u on the interior nodes
@@ -30,11 +35,15 @@ void launch_cell<float>(const LevelView<float>& lv, int op, Mode mode, float* u,
                         double* partial, cudaStream_t st);
 
 // FP32 surrogate smoother with shared-memory plane staging (stage.cu): the
-// four cell colour steps in one launch per sweep.  Supported when the
-// surrogate is fitted, u is 16-byte aligned and the plane ring fits in
-// shared memory; a bounded wait that gives up sets *lv.err.
-bool stage32_supported(const LevelView<float>& lv, const float* u);
-void launch_stage32_smooth(const LevelView<float>& lv, float* u, const float* f, cudaStream_t st);
+// four cell colour steps in one launch per sweep.  `cfg` (0 ..
+// STAGE32_CONFIGS - 1) picks the wavefront skew and the CTA size; a
+// configuration is supported when the surrogate is fitted, u is 16-byte
+// aligned and its plane ring fits in shared memory.  A bounded wait that
+// gives up sets *lv.err.
+constexpr int STAGE32_CONFIGS = 4;
+static_assert(STAGE32_CONFIGS <= STAGE32_CONFIGS_MAX, "tuner table too small");
+bool stage32_supported(const LevelView<float>& lv, const float* u, int cfg);
+void launch_stage32_smooth(const LevelView<float>& lv, float* u, const float* f, int cfg, cudaStream_t st);
 
 // FP64 surrogate line table (fit time): per cell the scale exponent E and,
 // per line (j, k), the q+1 coefficients of each of the 15 polynomials in i,
@@ -69,7 +78,7 @@ template <class T>
 void launch_low_step(const LevelView<T>& lv, const int* list, int n, T* u, const T* f, T* tmp, cudaStream_t st);
 
 template <class T>
-void launch_zero_list(const int* list, int n, T* v, cudaStream_t st);
+void launch_zero_list(const int* list, int n, T* v, int nrhs, int64_t vstride, cudaStream_t st);
 
 template <class T>
 void launch_prolong_add(const LevelView<T>& fine, const LevelView<T>& coarse, const int* low_par, const T* ec,
@@ -79,8 +88,9 @@ template <class T>
 void launch_restrict(const LevelView<T>& fine, const LevelView<T>& coarse, const int* coarse_low_fine,
                      const T* rf, T* rc, cudaStream_t st);
 
-// out[0] = sum of partial[0 .. n-1] (fixed order, one block).
-void launch_sum(const double* partial, int n, double* out, cudaStream_t st);
+// out[b] = sum of partial[b pstride .. b pstride + n - 1], b < nrhs (fixed
+// order, one block per right-hand side).
+void launch_sum(const double* partial, int n, int nrhs, int pstride, double* out, cudaStream_t st);
 
 template <class T>
 void launch_copy_cast(const double* src, T* dst, int64_t n, cudaStream_t st);
@@ -104,11 +114,18 @@ struct CoarseOp {                // exact operator of the N = 4 level
 // Assembles the interior rows and the inverse diagonal (setup).
 void launch_coarse_setup(const LevelView<double>& lv, CoarseOp& A, int* col, double* val, double* diag, double* dinv,
                          cudaStream_t st);
-// part needs 3 CG_BLOCKS doubles.
+// nrhs systems at once: vectors n_total apart, part 3 CG_BLOCKS doubles per
+// right-hand side, scalars rz / rr one per right-hand side (contiguous).
 void launch_cg_init(const CoarseOp& A, const double* f, double* x, double* r, double* z, double* p, double* part,
-                    double* rz_out, double* rr_out, cudaStream_t st);
+                    double* rz_out, double* rr_out, int nrhs, cudaStream_t st);
+// With rr_cur != nullptr (fixed-count iterations, e.g. inside a CUDA graph)
+// a right-hand side whose rr_cur <= 1e-26 ff is left unchanged and its
+// scalars are carried to rz_next / rr_out.
 void launch_cg_iteration(const CoarseOp& A, double* x, double* r, double* z, double* p, double* q, double* part,
-                         const double* rz_cur, double* rz_next, double* rr_out, cudaStream_t st);
+                         const double* rz_cur, double* rz_next, double* rr_out, int nrhs, cudaStream_t st,
+                         const double* rr_cur = nullptr, const double* ff = nullptr);
+// *flag = 1 when some rr[b] > 1e-26 ff[b].
+void launch_cg_check(const double* rr, const double* ff, int nrhs, int* flag, cudaStream_t st);
 
 // Lower-primitive stencil assembly (setup): pass 0 counts columns per row,
 // pass 1 fills the sliced ELL rows and the diagonal.

@@ -24,6 +24,7 @@ inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + thread
 // Halo: copy the owner value of every boundary point of every cell into the
 // cell's halo array (0 at Dirichlet points).  Stands where the paper's HHG
 // exchanges ghost layers between primitives (Sec. 4; Sec. 6).
+// Right-hand side blockIdx.y.
 template <class T>
 __global__ void halo_kernel(LevelView<T> lv, const T* __restrict__ u) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -31,7 +32,9 @@ __global__ void halo_kernel(LevelView<T> lv, const T* __restrict__ u) {
   const int c = (int)(t / lv.n_bnd), b = (int)(t % lv.n_bnd);
   const uint32_t p = lv.bnd_ijk[b];
   const int src = lv.halo_src[t];
-  lv.ghost[(int64_t)c * lv.n_full + lin_full(unpack_i(p), unpack_j(p), unpack_k(p), lv.N)] = src >= 0 ? u[src] : T(0);
+  const int64_t rb = blockIdx.y;
+  lv.ghost[rb * lv.gstride + (int64_t)c * lv.n_full + lin_full(unpack_i(p), unpack_j(p), unpack_k(p), lv.N)] =
+      src >= 0 ? u[rb * lv.vstride + src] : T(0);
 }
 
 template <class T>
@@ -47,9 +50,17 @@ __device__ __forceinline__ T low_row_offdiag(const LevelView<T>& lv, int64_t r, 
   return acc;
 }
 
+// Right-hand side blockIdx.y.
 template <class T, Mode MODE>
 __global__ void __launch_bounds__(LOW_THREADS) low_kernel(LevelView<T> lv, const T* __restrict__ u, T* __restrict__ out,
                                                         const T* __restrict__ f, double* partial) {
+  const int64_t rb = blockIdx.y;
+  u += rb * lv.vstride;
+  out += rb * lv.vstride;
+  if (MODE == RESIDUAL) {
+    f += rb * lv.vstride;
+    partial += rb * lv.pstride;
+  }
   double nrm = 0.0;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < lv.off_C; r += (int64_t)gridDim.x * blockDim.x) {
     const T d = lv.low_diag[r];
@@ -76,20 +87,25 @@ __global__ void low_step_kernel(LevelView<T> lv, const int* __restrict__ list, i
                                 const T* __restrict__ f, T* __restrict__ tmp) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
+  const int64_t rb = blockIdx.y;
+  u += rb * lv.vstride;
+  f += rb * lv.vstride;
+  tmp += rb * lv.tstride;
   const int r = list[t];
   tmp[t] = (f[r] - low_row_offdiag(lv, r, u)) / lv.low_diag[r];
 }
 
 template <class T>
-__global__ void scatter_kernel(const int* __restrict__ list, int n, const T* __restrict__ tmp, T* __restrict__ u) {
+__global__ void scatter_kernel(const int* __restrict__ list, int n, const T* __restrict__ tmp, T* __restrict__ u,
+                               int64_t tstride, int64_t vstride) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) u[list[t]] = tmp[t];
+  if (t < n) u[blockIdx.y * vstride + list[t]] = tmp[blockIdx.y * tstride + t];
 }
 
 template <class T>
-__global__ void zero_list_kernel(const int* __restrict__ list, int n, T* __restrict__ v) {
+__global__ void zero_list_kernel(const int* __restrict__ list, int n, T* __restrict__ v, int64_t vstride) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) v[list[t]] = T(0);
+  if (t < n) v[blockIdx.y * vstride + list[t]] = T(0);
 }
 
 // Parity of a fine point -> the coarse-edge direction it is the midpoint of
@@ -112,6 +128,10 @@ template <class T>
 __global__ void prolong_cell_kernel(LevelView<T> fine, LevelView<T> coarse, const T* __restrict__ ec, T* __restrict__ uf) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)fine.nC * fine.n_int) return;
+  const int64_t rb = blockIdx.y;
+  ec += rb * coarse.vstride;
+  uf += rb * fine.vstride;
+  coarse.ghost += rb * coarse.gstride;
   const int c = (int)(t / fine.n_int);
   const uint32_t p = fine.int_ijk[t % fine.n_int];
   const int I = unpack_i(p), J = unpack_j(p), K = unpack_k(p);
@@ -130,9 +150,11 @@ __global__ void prolong_cell_kernel(LevelView<T> fine, LevelView<T> coarse, cons
 
 template <class T>
 __global__ void prolong_low_kernel(LevelView<T> fine, const int* __restrict__ par, const T* __restrict__ ec,
-                                   T* __restrict__ uf) {
+                                   T* __restrict__ uf, int64_t cstride) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= fine.off_C) return;
+  ec += blockIdx.y * cstride;
+  uf += blockIdx.y * fine.vstride;
   if (fine.low_diag[r] == T(0)) return;
   const int a = par[2 * r], b = par[2 * r + 1];
   const T va = a >= 0 ? ec[a] : T(0);
@@ -148,6 +170,8 @@ template <class T>
 __global__ void restrict_cell_kernel(LevelView<T> fine, LevelView<T> coarse, const T* __restrict__ rf, T* __restrict__ rc) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)coarse.nC * coarse.n_int) return;
+  rf += blockIdx.y * fine.vstride;
+  rc += blockIdx.y * coarse.vstride;
   const int c = (int)(t / coarse.n_int);
   const uint32_t p = coarse.int_ijk[t % coarse.n_int];
   const int I = 2 * unpack_i(p), J = 2 * unpack_j(p), K = 2 * unpack_k(p);
@@ -165,6 +189,8 @@ __global__ void restrict_low_kernel(LevelView<T> fine, LevelView<T> coarse, cons
                                     const T* __restrict__ rf, T* __restrict__ rc) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= coarse.off_C) return;
+  rf += blockIdx.y * fine.vstride;
+  rc += blockIdx.y * coarse.vstride;
   const int fi = clf[r];
   if (fi < 0) { rc[r] = T(0); return; }
   const int64_t s = (int64_t)fi >> 5, lane = fi & 31;
@@ -177,11 +203,13 @@ __global__ void restrict_low_kernel(LevelView<T> fine, LevelView<T> coarse, cons
   rc[r] = fma(T(0.5), acc, rf[fi]);
 }
 
-__global__ void sum_kernel(const double* __restrict__ partial, int n, double* out) {
+// One block per right-hand side: out[b] = sum of its n partials.
+__global__ void sum_kernel(const double* __restrict__ partial, int n, int pstride, double* out) {
+  partial += (int64_t)blockIdx.x * pstride;
   double v = 0.0;
   for (int t = threadIdx.x; t < n; t += blockDim.x) v += partial[t];
   v = block_sum(v);
-  if (threadIdx.x == 0) out[0] = v;
+  if (threadIdx.x == 0) out[blockIdx.x] = v;
 }
 
 template <class T>
@@ -289,7 +317,7 @@ int low_blocks(int64_t rows) {
 template <class T>
 void launch_halo(const LevelView<T>& lv, const T* u, cudaStream_t st) {
   const int64_t n = (int64_t)lv.nC * lv.n_bnd;
-  halo_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(lv, u);
+  halo_kernel<T><<<dim3(grid_for(n, 256), lv.nrhs), 256, 0, st>>>(lv, u);
   HHG_CUDA(cudaGetLastError());
   count_launch();
 }
@@ -297,8 +325,9 @@ void launch_halo(const LevelView<T>& lv, const T* u, cudaStream_t st) {
 template <class T>
 void launch_low(const LevelView<T>& lv, Mode mode, const T* u, T* out, const T* f, double* partial, int nblk,
                 cudaStream_t st) {
-  if (mode == APPLY) low_kernel<T, APPLY><<<nblk, LOW_THREADS, 0, st>>>(lv, u, out, f, partial);
-  else low_kernel<T, RESIDUAL><<<nblk, LOW_THREADS, 0, st>>>(lv, u, out, f, partial);
+  const dim3 g(nblk, lv.nrhs);
+  if (mode == APPLY) low_kernel<T, APPLY><<<g, LOW_THREADS, 0, st>>>(lv, u, out, f, partial);
+  else low_kernel<T, RESIDUAL><<<g, LOW_THREADS, 0, st>>>(lv, u, out, f, partial);
   HHG_CUDA(cudaGetLastError());
   count_launch();
 }
@@ -306,16 +335,17 @@ void launch_low(const LevelView<T>& lv, Mode mode, const T* u, T* out, const T* 
 template <class T>
 void launch_low_step(const LevelView<T>& lv, const int* list, int n, T* u, const T* f, T* tmp, cudaStream_t st) {
   if (n == 0) return;
-  low_step_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(lv, list, n, u, f, tmp);
-  scatter_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(list, n, tmp, u);
+  const dim3 g(grid_for(n, 256), lv.nrhs);
+  low_step_kernel<T><<<g, 256, 0, st>>>(lv, list, n, u, f, tmp);
+  scatter_kernel<T><<<g, 256, 0, st>>>(list, n, tmp, u, lv.tstride, lv.vstride);
   HHG_CUDA(cudaGetLastError());
   count_launch(2);
 }
 
 template <class T>
-void launch_zero_list(const int* list, int n, T* v, cudaStream_t st) {
+void launch_zero_list(const int* list, int n, T* v, int nrhs, int64_t vstride, cudaStream_t st) {
   if (n == 0) return;
-  zero_list_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(list, n, v);
+  zero_list_kernel<T><<<dim3(grid_for(n, 256), nrhs), 256, 0, st>>>(list, n, v, vstride);
   HHG_CUDA(cudaGetLastError());
   count_launch();
 }
@@ -324,8 +354,9 @@ template <class T>
 void launch_prolong_add(const LevelView<T>& fine, const LevelView<T>& coarse, const int* low_par, const T* ec, T* uf,
                         cudaStream_t st) {
   const int64_t n = (int64_t)fine.nC * fine.n_int;
-  if (n) prolong_cell_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(fine, coarse, ec, uf);
-  prolong_low_kernel<T><<<grid_for(fine.off_C, 256), 256, 0, st>>>(fine, low_par, ec, uf);
+  if (n) prolong_cell_kernel<T><<<dim3(grid_for(n, 256), fine.nrhs), 256, 0, st>>>(fine, coarse, ec, uf);
+  prolong_low_kernel<T><<<dim3(grid_for(fine.off_C, 256), fine.nrhs), 256, 0, st>>>(fine, low_par, ec, uf,
+                                                                                    coarse.vstride);
   HHG_CUDA(cudaGetLastError());
   count_launch(n ? 2 : 1);
 }
@@ -334,14 +365,14 @@ template <class T>
 void launch_restrict(const LevelView<T>& fine, const LevelView<T>& coarse, const int* clf, const T* rf, T* rc,
                      cudaStream_t st) {
   const int64_t n = (int64_t)coarse.nC * coarse.n_int;
-  if (n) restrict_cell_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(fine, coarse, rf, rc);
-  restrict_low_kernel<T><<<grid_for(coarse.off_C, 256), 256, 0, st>>>(fine, coarse, clf, rf, rc);
+  if (n) restrict_cell_kernel<T><<<dim3(grid_for(n, 256), fine.nrhs), 256, 0, st>>>(fine, coarse, rf, rc);
+  restrict_low_kernel<T><<<dim3(grid_for(coarse.off_C, 256), fine.nrhs), 256, 0, st>>>(fine, coarse, clf, rf, rc);
   HHG_CUDA(cudaGetLastError());
   count_launch(n ? 2 : 1);
 }
 
-void launch_sum(const double* partial, int n, double* out, cudaStream_t st) {
-  sum_kernel<<<1, 1024, 0, st>>>(partial, n, out);
+void launch_sum(const double* partial, int n, int nrhs, int pstride, double* out, cudaStream_t st) {
+  sum_kernel<<<nrhs, 1024, 0, st>>>(partial, n, pstride, out);
   HHG_CUDA(cudaGetLastError());
   count_launch();
 }
@@ -374,7 +405,7 @@ void launch_low_assemble(const LevelView<double>& lv, int pass, const int64_t* i
   template void launch_halo<T>(const LevelView<T>&, const T*, cudaStream_t);                                      \
   template void launch_low<T>(const LevelView<T>&, Mode, const T*, T*, const T*, double*, int, cudaStream_t);    \
   template void launch_low_step<T>(const LevelView<T>&, const int*, int, T*, const T*, T*, cudaStream_t);        \
-  template void launch_zero_list<T>(const int*, int, T*, cudaStream_t);                                           \
+  template void launch_zero_list<T>(const int*, int, T*, int, int64_t, cudaStream_t);                             \
   template void launch_prolong_add<T>(const LevelView<T>&, const LevelView<T>&, const int*, const T*, T*,         \
                                       cudaStream_t);                                                              \
   template void launch_restrict<T>(const LevelView<T>&, const LevelView<T>&, const int*, const T*, T*,            \

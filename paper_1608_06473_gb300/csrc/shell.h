@@ -4,12 +4,15 @@
 #pragma once
 
 #include <cstdint>
+#include <tuple>
 #include <vector>
 
 #include "common.h"
 #include "mesh.h"
 
 namespace hhg {
+
+constexpr int STAGE32_CONFIGS_MAX = 4;  // staged FP32 smoother configurations (stage.cu)
 
 // Geometry of one macro cell: its 4 vertices (ascending global id) and the
 // radii that rho interpolates (Sec. 2.2, blending map Phi).
@@ -47,6 +50,9 @@ struct LevelView {
   const CellGeom* geom;          // [nC]
   const uint32_t* plane_nodes;   // interior points (packed) by (k, colour), deep-interior ones first
   const int* plane_off;          // start of (k, colour) in plane_nodes, [4 (N + 1) + 1]
+  const int* plane_x;            // [n_plane] position of each listed point within its plane
+  const int* plane_nb;           // [14 * n_plane] neighbour codes of the points next to the cell boundary
+  int n_plane;
   const uint32_t* int_ijk;       // [n_int] interior points in canonical order
   const uint32_t* bnd_ijk;       // [n_bnd] boundary points of a cell
   const int* bnd_slot;           // [n_full] boundary slot of a cell-local point, -1 = interior
@@ -70,6 +76,13 @@ struct LevelView {
   const T* sell_val;
   const T* low_diag;             // [off_C]
   int* err;                      // device error word: set to 1 when a bounded wait gives up
+  int smooth_cfg;                // FP32 surrogate smoother: -1 = per-colour node kernel, else staged configuration
+  // right-hand sides processed together: vector b of a level lives at
+  // v + b vstride, its halo copy at ghost + b gstride, its residual partials
+  // at partial + b pstride, its lower-step buffer at tmp + b tstride
+  int nrhs;
+  int64_t vstride, gstride;
+  int pstride, tstride;
 };
 
 struct Level {
@@ -81,6 +94,9 @@ struct Level {
   int* d_halo_src = nullptr;
   uint32_t* d_plane_nodes = nullptr;
   int* d_plane_off = nullptr;
+  int* d_plane_x = nullptr;
+  int* d_plane_nb = nullptr;
+  int n_plane = 0;
   std::vector<int> h_plane_off;
   uint32_t* d_int_ijk = nullptr;
   // lower primitives
@@ -110,6 +126,10 @@ struct Level {
   uint32_t* d_colour_nodes = nullptr;
   uint32_t* d_all_nodes = nullptr;
   int colour_off[5] = {0, 0, 0, 0, 0};
+  // FP32 surrogate smoother chosen by the tuner (-2 = not tuned, -1 = per-colour
+  // node kernel, >= 0 = staged configuration) and the candidates' times (ms)
+  int tune32 = -2;
+  double tune32_ms[1 + STAGE32_CONFIGS_MAX] = {};
   // halo copies and work vectors (allocated on demand)
   double* d_ghost64 = nullptr;
   float* d_ghost32 = nullptr;
@@ -148,6 +168,40 @@ struct hhg_shell {
   int64_t red_len = 0;
   double* d_cg = nullptr;              // coarse-solver vectors
   int* d_err = nullptr;                // device error word of the staged kernels (0 = ok)
+  // batches: work vectors, halo copies, step buffers, reduction and coarse
+  // solver scratch hold `cap` right-hand sides; `nb` of them are active in
+  // the current call
+  int cap = 1;
+  int nb = 1;
+  // CUDA-graph V-cycles: the captured cycle of the last key, the
+  // coarse-solver iteration count it was captured with, and a generation
+  // counter bumped whenever captured kernels or buffers change
+  bool graphs = true;
+  int64_t gen = 0;
+  int cg_fixed = 0;          // > 0 while capturing: fixed-count coarse iterations
+  int cg_graph_iters = 0;    // iterations the next capture uses
+  int cg_last = 0;           // iterations of the last host-driven coarse solve
+  struct GraphKey {
+    const void* f;
+    const void* u;
+    int nb, op, dtype, nu1, nu2, iters;
+    int64_t gen;
+    bool operator==(const GraphKey& o) const {
+      return f == o.f && u == o.u && nb == o.nb && op == o.op && dtype == o.dtype && nu1 == o.nu1 && nu2 == o.nu2 &&
+             iters == o.iters && gen == o.gen;
+    }
+  } graph_key{};
+  cudaGraphExec_t graph_exec = nullptr;
+  bool capturing = false;
+  int64_t graph_launches = 0;          // kernels in the captured cycle (counted again per replay)
+  // timed scopes captured into the graph (class, begin, end): re-recorded by
+  // every replay and accumulated after it into gsum / gcnt
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> gtimed;
+  double gsum[HHG_T_COUNT] = {};
+  int64_t gcnt[HHG_T_COUNT] = {};
+  cudaStream_t gstream = nullptr;      // capture and replay stream of the graphs
+  cudaEvent_t gev[2] = {nullptr, nullptr};
+  int pstride = 0;                     // residual partials per right-hand side
   void* coarse_op = nullptr;           // hhg::CoarseOp of the N = 4 level (owned)
   double* d_stage[3] = {nullptr, nullptr, nullptr};  // staging for host-pointer arguments
   bool f32_ready = false;              // FP32 resources allocated

@@ -32,54 +32,101 @@ namespace hhg {
 
 namespace {
 
-constexpr int RING = 7;  // u planes s-3 .. s+2 in use during step s, plus s+3 in flight
-constexpr int CTAB = 5;  // coefficient tables of planes s-2 .. s+1 in use, s+2 being filled
+// Colour c of plane k is updated in step s = k - 1 + SKEW c.  SKEW = 1 is the
+// tightest wavefront (colour c - 1 on plane k + 1 is updated earlier in the
+// same step, so the step needs a barrier after each colour); SKEW = 2 moves
+// every dependency of a step into earlier steps, so the four colour tasks of a
+// step are independent and share one barrier, at the cost of a wider ring.
+template <int SKEW>
+struct Sched {
+  static constexpr int RING = 3 * SKEW + 4;  // u planes s - 3 SKEW .. s + 2 in use, s + 3 in flight
+  static constexpr int CTAB = 3 * SKEW + 2;  // tables of planes s + 1 - 3 SKEW .. s + 1 in use, s + 2 filled
+};
 
 __host__ __device__ inline int plane_size(int N, int k) { return (N - 2 - k) * (N - 1 - k) / 2; }
 // Floats per ring slot: plane 1 (the largest) at an offset of up to 3 floats
 // (the slot keeps the plane's global 16-byte phase), rounded up to 16 bytes.
 __host__ __device__ inline int slot_floats(int N) { return (plane_size(N, 1) + 3 + 3) & ~3; }
 
+// Per-plane coefficients of the FP32 surrogate, paired by direction for
+// packed FP32 arithmetic: pair m holds directions 2m and 2m + 1 (the centre,
+// 14, is paired with zeros), NPP2 float2 per pair (a multiple of 16 bytes).
 template <int Q>
+__host__ __device__ constexpr int npp2() { return ((Q + 1) * (Q + 2) / 2 + 1) / 2 * 2; }
+constexpr int NPAIR = 8;
+
+template <int Q, int SKEW>
 size_t stage_smem(int N) {
-  return sizeof(float) * ((size_t)RING * slot_floats(N) + (size_t)CTAB * 15 * np_pad<Q>()) + sizeof(uint64_t) * RING;
+  return sizeof(float) * (size_t)Sched<SKEW>::RING * slot_floats(N) +
+         sizeof(float2) * (size_t)Sched<SKEW>::CTAB * NPAIR * npp2<Q>() + sizeof(uint64_t) * Sched<SKEW>::RING +
+         sizeof(int) * 2 * (size_t)(N + 2);
 }
 
 // Resident CTAs per SM the register budget is sized for (64 registers a thread).
 template <int THREADS>
 constexpr int stage_min_blocks() { return THREADS >= 1024 ? 1 : 1024 / THREADS; }
 
-template <int Q, int THREADS>
-__global__ void __launch_bounds__(THREADS, stage_min_blocks<THREADS>()) lsqp_stage32_smooth(LevelView<float> lv, float* u, const float* f,
-                                                                int* err) {
+// n / d in FP32: the hardware reciprocal estimate refined by one
+// Newton-Raphson step x <- x + x (1 - d x), then the product.
+__device__ __forceinline__ float div_nr32(float n, float d) {
+  float x;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(x) : "f"(d));
+  x = fmaf(x, fmaf(-d, x, 1.0f), x);
+  return n * x;
+}
+
+// Two directions' polynomials in (i, j) at once (packed FP32 FMA).
+template <int Q>
+__device__ __forceinline__ float2 eval_plane2(const float2* P, float2 I, float2 J) {
+  float2 s = make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int a = Q; a >= 0; --a) {
+    float2 c = P[plane_index<Q>(a, Q - a)];
+#pragma unroll
+    for (int b = Q - a - 1; b >= 0; --b) c = __ffma2_rn(c, J, P[plane_index<Q>(a, b)]);
+    s = (a == Q) ? c : __ffma2_rn(s, I, c);
+  }
+  return s;
+}
+
+template <int Q, int THREADS, int SKEW>
+__global__ void __launch_bounds__(THREADS, stage_min_blocks<THREADS>()) lsqp_stage32_smooth(LevelView<float> lv,
+                                                                                       float* u, const float* f,
+                                                                                       int* err) {
+  constexpr int RING = Sched<SKEW>::RING, CTAB = Sched<SKEW>::CTAB;
   constexpr int NP = (Q + 1) * (Q + 2) / 2;
-  constexpr int NPP = np_pad<Q>();
-  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int NP2 = npp2<Q>();
+  extern __shared__ __align__(16) float smem[];
   const int N = lv.N, np = N - 3, S = slot_floats(N);
-  float* ring = reinterpret_cast<float*>(smem);
-  float* ctab = ring + RING * S;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(ctab + CTAB * 15 * NPP);
+  float* ring = smem;
+  float2* ctab = reinterpret_cast<float2*>(ring + RING * S);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(ctab + CTAB * NPAIR * NP2);
+  int* porg = reinterpret_cast<int*>(bar + RING);  // [N + 2]: ring offset of the first node of plane k
+  int* pst = porg + (N + 2);                       // [N + 2]: position of that node in the cell's block
   const int c = blockIdx.x;
   const int64_t cbase = lv.off_C + (int64_t)c * lv.n_int;
   const float* tab = lv.plane32 + (int64_t)c * np * 15 * NP;
   const float* ghost = lv.ghost + (int64_t)c * lv.n_full;
+  const int n_plane = lv.n_plane;
   bool failed = false;
 
-  // first interior node of plane k within the cell's block, and the
-  // shared-memory position of that node (the slot keeps the 16-byte phase)
-  auto pstart = [&](int k) { return lin_interior32(1, 1, k, N); };
-  auto slot = [](int k) { return (k - 1) % RING; };  // planes 1..7 take slots 0..6, 8..14 reuse them
-  auto origin = [&](int k) { return ring + slot(k) * S + (int)((cbase + pstart(k)) & 3); };
-
+  // the slot keeps the plane's 16-byte phase in the vector; planes 0 and
+  // np + 1 have no interior points (their entries are never read)
+  for (int k = threadIdx.x; k <= N + 1; k += THREADS) {
+    const int ps = (k >= 1 && k <= np) ? lin_interior32(1, 1, k, N) : 0;
+    pst[k] = ps;
+    porg[k] = (k >= 1 && k <= np) ? ((k - 1) % RING) * S + (int)((cbase + ps) & 3) : 0;
+  }
   if (threadIdx.x == 0)
     for (int r = 0; r < RING; ++r) mbar_init(&bar[r], 1);
   __syncthreads();
+  auto slot = [](int k) { return (k - 1) % RING; };
 
   auto issue = [&](int k) {
     if (k < 1 || k > np) return;
-    const int64_t g0 = cbase + pstart(k), g1 = g0 + plane_size(N, k);
+    const int64_t g0 = cbase + pst[k], g1 = g0 + plane_size(N, k);
     const int64_t a0 = (g0 + 3) & ~(int64_t)3, a1 = g1 & ~(int64_t)3;
-    float* o = origin(k);
+    float* o = ring + porg[k];
     if (threadIdx.x == 0) {
       const uint32_t bytes = a1 > a0 ? (uint32_t)((a1 - a0) * 4) : 0u;
       fence_proxy_async_smem();
@@ -95,18 +142,18 @@ __global__ void __launch_bounds__(THREADS, stage_min_blocks<THREADS>()) lsqp_sta
   };
   auto writeback = [&](int k) {
     if (k < 1 || k > np) return;
-    const int64_t g0 = cbase + pstart(k);
-    const float* o = origin(k);
+    float* dst = u + cbase + pst[k];
+    const float* o = ring + porg[k];
     const int n = plane_size(N, k);
-    for (int x = threadIdx.x; x < n; x += THREADS) u[g0 + x] = o[x];
+    for (int x = threadIdx.x; x < n; x += THREADS) dst[x] = o[x];
   };
   auto load_tab = [&](int k) {
     if (k < 1 || k > np) return;
-    float* d = ctab + ((k - 1) % CTAB) * 15 * NPP;
+    float* d = reinterpret_cast<float*>(ctab + ((k - 1) % CTAB) * NPAIR * NP2);
     const float* s = tab + (int64_t)(k - 1) * 15 * NP;
-    for (int t = threadIdx.x; t < 15 * NPP; t += THREADS) {
-      const int e = t % NPP, w = t / NPP;
-      d[t] = e < NP ? s[w * NP + e] : 0.0f;
+    for (int t = threadIdx.x; t < NPAIR * NP2 * 2; t += THREADS) {
+      const int h = t & 1, e = (t >> 1) % NP2, m = (t >> 1) / NP2, w = 2 * m + h;
+      d[t] = (e < NP && w < 15) ? s[w * NP + e] : 0.0f;
     }
   };
   auto wait_plane = [&](int k) {
@@ -115,73 +162,90 @@ __global__ void __launch_bounds__(THREADS, stage_min_blocks<THREADS>()) lsqp_sta
     if (!mbar_wait(&bar[slot(k)], (uint32_t)(((k - 1) / RING) & 1))) failed = true;
   };
 
-  // colour cc on plane k (all its neighbours are resident)
-  auto process = [&](int k, int cc) {
-    const int beg = lv.plane_off[k * 4 + cc], end = lv.plane_off[k * 4 + cc + 1];
-    const float* P = ctab + ((k - 1) % CTAB) * 15 * NPP;
-    float* om = origin(k);
-    const float* ot = origin(k + 1);  // used only for interior neighbours (k + 1 <= np)
-    const float* ob = origin(k - 1);  // used only for interior neighbours (k - 1 >= 1)
-    const int pk = pstart(k);
-    const float* fk = f + cbase + pk;
-    for (int t = beg + (int)threadIdx.x; t < end; t += THREADS) {
-      const uint32_t p = lv.plane_nodes[t];
-      const int i = unpack_i(p), j = unpack_j(p);
-      const int x = lin_interior32(i, j, k, N) - pk;
-      const float fi = (float)i, fj = (float)j;
-      auto wt = [&](int w) -> float {
-        float Pw[NPP];
+  // Eq. 5.1 at list entry e of plane k (all neighbours resident)
+  auto update = [&](int k, int e, float fv, uint32_t p, int x) {
+    const float2* P = ctab + ((k - 1) % CTAB) * NPAIR * NP2;
+    const int om = porg[k];
+    const int i = unpack_i(p), j = unpack_j(p);
+    const float2 I = make_float2((float)i, (float)i), J = make_float2((float)j, (float)j);
+    auto body = [&](auto nb) {
+      float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int v = 0; v < NPP; v += 4) {
-          const float4 q4 = *reinterpret_cast<const float4*>(P + w * NPP + v);
-          Pw[v] = q4.x;
-          Pw[v + 1] = q4.y;
-          Pw[v + 2] = q4.z;
-          Pw[v + 3] = q4.w;
-        }
-        return eval_plane<float, Q>(Pw, fi, fj);
-      };
-      auto update = [&](auto nb) {
-        float a0 = fk[x], a1 = 0.0f;
-#pragma unroll
-        for (int w = 0; w < 14; w += 2) {
-          a0 = fmaf(-wt(w), nb(w), a0);
-          a1 = fmaf(-wt(w + 1), nb(w + 1), a1);
-        }
-        om[x] = (a0 + a1) / wt(MC);
-      };
-      if (deep_interior(i, j, k, N)) {
-        // plane-local offsets: L = length of line j in plane k; a node (i, j)
-        // of plane k + 1 sits j - 1 places before (i, j) of plane k
-        const int L = N - 1 - j - k;
-        update([&](int w) -> float {
-          switch (w) {
-            case ME: return om[x + 1];
-            case MW: return om[x - 1];
-            case MN: return om[x + L];
-            case MS: return om[x - L - 1];
-            case MNW: return om[x + L - 1];
-            case MSE: return om[x - L];
-            case TC: return ot[x - j + 1];
-            case TW: return ot[x - j];
-            case TS: return ot[x - L - j + 1];
-            case TSE: return ot[x - L - j + 2];
-            case BC: return ob[x + j - 1];
-            case BE: return ob[x + j];
-            case BN: return ob[x + L + j];
-            default: return ob[x + L + j - 1];  // BNW
-          }
-        });
-      } else {
-        update([&](int w) -> float {
-          const int i2 = i + DI(w), j2 = j + DJ(w), k2 = k + DK(w);
-          if (is_interior(i2, j2, k2, N)) {
-            const float* o = DK(w) > 0 ? ot : (DK(w) < 0 ? ob : om);
-            return o[lin_interior32(i2, j2, k2, N) - pstart(k2)];
-          }
-          return ghost[lin_full(i2, j2, k2, N)];
-        });
+      for (int m = 0; m < 7; ++m) {
+        const float2 w2 = eval_plane2<Q>(P + m * NP2, I, J);
+        acc = __ffma2_rn(w2, make_float2(nb(2 * m), nb(2 * m + 1)), acc);
       }
+      const float wc = eval_plane2<Q>(P + 7 * NP2, I, J).x;
+      ring[om + x] = div_nr32(fv - acc.x - acc.y, wc);
+    };
+    if (deep_interior(i, j, k, N)) {
+      // L = length of line j in plane k; node (i, j) of plane k + 1 sits
+      // j - 1 places before node (i, j) of plane k, of plane k - 1 j - 1 after
+      const float* pm = ring + om + x;
+      const float* pt = ring + porg[k + 1] + x - j;
+      const float* pb = ring + porg[k - 1] + x + j;
+      const int L = N - 1 - j - k;
+      body([&](int w) -> float {
+        switch (w) {
+          case ME: return pm[1];
+          case MW: return pm[-1];
+          case MN: return pm[L];
+          case MS: return pm[-L - 1];
+          case MNW: return pm[L - 1];
+          case MSE: return pm[-L];
+          case TC: return pt[1];
+          case TW: return pt[0];
+          case TS: return pt[1 - L];
+          case TSE: return pt[2 - L];
+          case BC: return pb[-1];
+          case BE: return pb[0];
+          case BN: return pb[L];
+          default: return pb[L - 1];  // BNW
+        }
+      });
+    } else {
+      body([&](int w) -> float {
+        const int code = lv.plane_nb[w * n_plane + e];
+        if (code < 0) return ghost[code & 0x7fffffff];
+        return ring[porg[k + (code >> 29) - 1] + (code & 0x1fffffff)];
+      });
+    }
+  };
+
+  // the colour tasks of step s: colour cc on plane s + 1 - SKEW cc, taken as
+  // one pool of list entries (SKEW = 2) or one task per barrier (SKEW = 1)
+  auto run_tasks = [&](int s, int c0, int c1) {
+    int b0 = 0, b1 = 0, b2 = 0, b3 = 0, p1, p2, p3, p4;  // task starts in the lists; pool prefix sums
+    auto task = [&](int cc, int& b) {
+      const int k = s + 1 - SKEW * cc;
+      if (cc < c0 || cc >= c1 || k < 1 || k > np) return 0;
+      b = lv.plane_off[k * 4 + cc];
+      return lv.plane_off[k * 4 + cc + 1] - b;
+    };
+    p1 = task(0, b0);
+    p2 = p1 + task(1, b1);
+    p3 = p2 + task(2, b2);
+    p4 = p3 + task(3, b3);
+    constexpr int B = 2;  // entries per thread in flight
+    for (int base = threadIdx.x; base < p4; base += B * THREADS) {
+      int e[B], kk[B], x[B];
+      uint32_t p[B];
+      float fv[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const int idx = base + b * THREADS;
+        const int cc = (idx >= p1) + (idx >= p2) + (idx >= p3);
+        const int start = cc == 0 ? b0 : (cc == 1 ? b1 - p1 : (cc == 2 ? b2 - p2 : b3 - p3));
+        kk[b] = s + 1 - SKEW * cc;
+        e[b] = idx < p4 ? start + idx : -1;
+        p[b] = e[b] >= 0 ? lv.plane_nodes[e[b]] : 0u;
+        x[b] = e[b] >= 0 ? lv.plane_x[e[b]] : 0;
+      }
+#pragma unroll
+      for (int b = 0; b < B; ++b) fv[b] = e[b] >= 0 ? f[cbase + pst[kk[b]] + x[b]] : 0.0f;
+#pragma unroll
+      for (int b = 0; b < B; ++b)
+        if (e[b] >= 0) update(kk[b], e[b], fv[b], p[b], x[b]);
     }
   };
 
@@ -192,65 +256,86 @@ __global__ void __launch_bounds__(THREADS, stage_min_blocks<THREADS>()) lsqp_sta
   wait_plane(1);
   cp_async_wait_all();
   __syncthreads();
-  for (int s = 0; s <= np + 3; ++s) {
-    writeback(s - 3);  // final since step s - 1
-    issue(s + 3);      // into the slot of plane s - 4, free since step s - 1
+  for (int s = 0; s <= np + 3 * SKEW; ++s) {
+    writeback(s - 3 * SKEW);  // colour 3 done in step s - 1
+    issue(s + 3);             // into the slot of plane s + 3 - RING, last read in step s - 1
     load_tab(s + 2);
     cp_async_commit();
     wait_plane(s + 2);
+    if (SKEW == 1) {
 #pragma unroll 1
-    for (int cc = 0; cc < 4; ++cc) {
-      const int k = s + 1 - cc;
-      if (k >= 1 && k <= np) process(k, cc);
-      if (cc == 3) cp_async_wait_all();
+      for (int cc = 0; cc < 4; ++cc) {
+        run_tasks(s, cc, cc + 1);
+        if (cc == 3) cp_async_wait_all();
+        __syncthreads();
+      }
+    } else {
+      run_tasks(s, 0, 4);
+      cp_async_wait_all();
       __syncthreads();
     }
   }
   if (failed) atomicExch(err, 1);
 }
 
-template <int Q, int THREADS>
+template <int Q, int THREADS, int SKEW>
 void launch_q(const LevelView<float>& lv, float* u, const float* f, int* err, cudaStream_t st) {
-  const size_t smem = stage_smem<Q>(lv.N);
-  auto kern = lsqp_stage32_smooth<Q, THREADS>;
-  HHG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t smem = stage_smem<Q, SKEW>(lv.N);
+  auto kern = lsqp_stage32_smooth<Q, THREADS, SKEW>;
+  ensure_smem_limit((const void*)kern, smem);
   kern<<<lv.nC, THREADS, smem, st>>>(lv, u, f, err);
   HHG_CUDA(cudaGetLastError());
   count_launch();
 }
 
+int optin_smem() {
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+  return optin;
+}
+
+// Launch configurations the tuner chooses from: (SKEW, threads per CTA).
+struct Cfg {
+  int skew, threads;
+};
+constexpr Cfg kCfgs[STAGE32_CONFIGS] = {{1, 256}, {1, 1024}, {2, 128}, {2, 512}};
+
 template <int Q>
-void launch_t(const LevelView<float>& lv, float* u, const float* f, int* err, cudaStream_t st) {
-  if (lv.N >= 128)
-    launch_q<Q, 1024>(lv, u, f, err, st);
-  else if (lv.N >= 64)
-    launch_q<Q, 256>(lv, u, f, err, st);
-  else
-    launch_q<Q, 128>(lv, u, f, err, st);
+size_t cfg_smem(int cfg, int N) {
+  return kCfgs[cfg].skew == 1 ? stage_smem<Q, 1>(N) : stage_smem<Q, 2>(N);
+}
+
+template <int Q>
+void launch_cfg(int cfg, const LevelView<float>& lv, float* u, const float* f, int* err, cudaStream_t st) {
+  switch (cfg) {
+    case 0: launch_q<Q, 256, 1>(lv, u, f, err, st); break;
+    case 1: launch_q<Q, 1024, 1>(lv, u, f, err, st); break;
+    case 2: launch_q<Q, 128, 2>(lv, u, f, err, st); break;
+    default: launch_q<Q, 512, 2>(lv, u, f, err, st); break;
+  }
+}
+
+size_t smem_of(int q, int cfg, int N) {
+  return q == 1 ? cfg_smem<1>(cfg, N) : (q == 2 ? cfg_smem<2>(cfg, N) : cfg_smem<3>(cfg, N));
 }
 
 }  // namespace
 
-bool stage32_supported(const LevelView<float>& lv, const float* u) {
-  if (lv.q < 1 || lv.q > 3 || lv.N < 8 || lv.plane32 == nullptr || lv.err == nullptr) return false;
+bool stage32_supported(const LevelView<float>& lv, const float* u, int cfg) {
+  if (cfg < 0 || cfg >= STAGE32_CONFIGS) return false;
+  if (lv.q < 1 || lv.q > 3 || lv.N < 8 || lv.plane32 == nullptr || lv.err == nullptr || lv.plane_nb == nullptr)
+    return false;
   if (reinterpret_cast<uintptr_t>(u) & 15) return false;
-  size_t smem = 0;
-  switch (lv.q) {
-    case 1: smem = stage_smem<1>(lv.N); break;
-    case 2: smem = stage_smem<2>(lv.N); break;
-    default: smem = stage_smem<3>(lv.N); break;
-  }
-  int dev = 0, optin = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return false;
-  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
-  return smem <= (size_t)optin;
+  static const int optin = optin_smem();
+  return smem_of(lv.q, cfg, lv.N) <= (size_t)optin;
 }
 
-void launch_stage32_smooth(const LevelView<float>& lv, float* u, const float* f, cudaStream_t st) {
+void launch_stage32_smooth(const LevelView<float>& lv, float* u, const float* f, int cfg, cudaStream_t st) {
   switch (lv.q) {
-    case 1: launch_t<1>(lv, u, f, lv.err, st); break;
-    case 2: launch_t<2>(lv, u, f, lv.err, st); break;
-    case 3: launch_t<3>(lv, u, f, lv.err, st); break;
+    case 1: launch_cfg<1>(cfg, lv, u, f, lv.err, st); break;
+    case 2: launch_cfg<2>(cfg, lv, u, f, lv.err, st); break;
+    case 3: launch_cfg<3>(cfg, lv, u, f, lv.err, st); break;
     default: throw Error{HHG_ENOTFIT, "surrogate degree not fitted"};
   }
 }

@@ -32,3 +32,20 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, n), n
     assert set(declared()) <= set(hhg.exported_symbols())
     assert hhg.hhg_last_error() == ""
+
+
+def test_problem_node_counts_match_the_mesh():
+    """hhg_problem_nodes (host formula, no GPU): (N_r + 1)(10 n_t^2 + 2)
+    nodes, the two boundary spheres Dirichlet -- against the oracle's mesh."""
+    import paper_1608_06473_gb300 as hhg
+    from oracle import mesh as M
+    if not os.path.exists(hhg.LIB_PATH):
+        from paper_1608_06473_gb300 import _build
+        _build.build()
+    for tang, layers, L in [(0, 1, 2), (0, 1, 4), (1, 2, 3), (2, 4, 3)]:
+        sh = M.make_shell(tang=tang, layers=layers)
+        lv = M.make_level(sh, 2 ** L)
+        assert hhg.hhg_problem_nodes(0.45, 1.0, tang, layers, L) == (lv.n_total, len(lv.free))
+    assert hhg.hhg_problem_nodes(0.55, 1.0, 2, 4, 6) == (168428034, 167117310)
+    with pytest.raises(hhg.HHGError):
+        hhg.hhg_problem_nodes(0.55, 1.0, 0, 1, 1)
