@@ -309,7 +309,8 @@ def run_ours(args, rank, world, local):
         cfg = hhg.hhg_tuning(s.handle, L)[0]
         kname = ("lsqp_stage32_smooth<%d> (finest level, one launch per sweep, planes staged in shared memory; "
                  "tuned configuration %d)" % (args.q, cfg)) if cfg >= 0 else \
-            "lsqp_node32_kernel<%d,SMOOTH> (finest level, tuned: one launch per colour)" % args.q
+            ("lsqp_node32_%skernel<%d,SMOOTH> (finest level, tuned: one launch per colour)"
+             % ("x2_" if cfg == -2 else "", args.q))
         roofline = {"kernel": kname,
                     "bound": "hbm", "achieved": achieved, "peak": HBM_MEASURED_GBS, "unit": "GB/s",
                     "frac": achieved / HBM_MEASURED_GBS,

@@ -301,14 +301,17 @@ hhg_status hhg_timing_read(hhg_shell* shell, int which, double* total_ms, int64_
 /* Launch configuration the tuner chose for the FP32 surrogate smoother on
  * level L (the tuner times the candidates on the device once the FP32
  * buffers exist and after every fit): *cfg = -1 for the per-colour
- * thread-per-node kernel, 0..3 for the shared-memory staged one-launch
- * kernel with (wavefront skew, threads per CTA) = (1, 256), (1, 1024),
- * (2, 128), (2, 512); -2 if not tuned.  ms (nullable, 5 entries) receives
- * each candidate's best time for one cell sweep (-1 = not run). */
+ * thread-per-node kernel, -2 for the same with two nodes per thread in
+ * flight, 0..3 for the shared-memory staged one-launch kernel with
+ * (wavefront skew, threads per CTA) = (1, 256), (1, 1024), (2, 128),
+ * (2, 512); -9 if not tuned.  ms (nullable, 6 entries) receives each
+ * candidate's best time for one cell sweep, candidate cfg at ms[cfg + 2]
+ * (-1 = not run).  The FP32 apply and residual use the two-nodes variant
+ * when the smoother does. */
 hhg_status hhg_tuning(const hhg_shell* shell, int L, int* cfg, double* ms);
 
-/* Pins the FP32 surrogate smoother of level L to configuration cfg (-1 or a
- * staged configuration 0..3 as above) until the next fit; a staged
+/* Pins the FP32 surrogate smoother of level L to configuration cfg (-2, -1
+ * or a staged configuration 0..3 as above) until the next fit; a staged
  * configuration that does not fit the level falls back to the per-colour
  * kernel at launch.  HHG_EINVAL for an unknown cfg. */
 hhg_status hhg_set_tuning(hhg_shell* shell, int L, int cfg);

@@ -147,7 +147,7 @@ def hhg_timing_read(shell: int, which: int):
 def hhg_tuning(shell: int, L: int):
     """(chosen FP32 smoother configuration, per-candidate ms) of level L."""
     cfg = ctypes.c_int()
-    ms = np.zeros(5)
+    ms = np.zeros(6)
     _check(lib().hhg_tuning(shell, L, ctypes.byref(cfg), ms.ctypes.data))
     return cfg.value, ms
 

@@ -254,12 +254,21 @@ static void build_level(hhg_shell* s, int n, cudaStream_t st) {
         (m.face_dirichlet((int)f) ? dirl : steps[3 + (p + 2 * q) % 3]).push_back((int)idx);
       }
   L.n_free = lay.n_total - (int64_t)dirl.size();
+  // the lower rows are stored in step order (steps 1-6, then the Dirichlet
+  // rows): a smoother step reads one contiguous range of the sliced rows
+  std::vector<int> perm, pos((size_t)lay.off_C, -1);
   L.max_step = 0;
   for (int t = 0; t < 6; ++t) {
+    L.step_beg[t] = (int)perm.size();
     L.step_n[t] = (int)steps[t].size();
     L.max_step = std::max(L.max_step, L.step_n[t]);
-    L.d_step[t] = upload(A, steps[t], st);
+    perm.insert(perm.end(), steps[t].begin(), steps[t].end());
   }
+  perm.insert(perm.end(), dirl.begin(), dirl.end());
+  HHG_CHECK((int64_t)perm.size() == lay.off_C, HHG_EINVAL, "lower rows do not partition into smoother steps");
+  for (int64_t p = 0; p < lay.off_C; ++p) pos[perm[p]] = (int)p;
+  L.d_low_perm = upload(A, perm, st);
+  L.d_low_pos = upload(A, pos, st);
   L.n_dirichlet = (int)dirl.size();
   L.d_dirichlet = upload(A, dirl, st);
 
@@ -280,6 +289,7 @@ static void build_level(hhg_shell* s, int n, cudaStream_t st) {
   v.N = N; v.nC = (int)lay.nC; v.off_E = lay.off_E; v.off_F = lay.off_F; v.off_C = lay.off_C;
   v.n_total = lay.n_total; v.n_int = lay.n_int; v.n_full = lay.n_full; v.n_bnd = L.n_bnd;
   v.geom = s->d_geom; v.bnd_ijk = L.d_bnd_ijk; v.bnd_slot = L.d_bnd_slot; v.halo_src = L.d_halo_src;
+  v.low_perm = L.d_low_perm; v.low_pos = L.d_low_pos;
   int64_t* d_inc_ptr = upload(A, inc_ptr, st);
   int* d_inc_cb = upload(A, inc_cb, st);
   int* d_len = A.alloc_n<int>((size_t)std::max<int64_t>(lay.off_C, 1));
@@ -291,7 +301,8 @@ static void build_level(hhg_shell* s, int n, cudaStream_t st) {
   std::vector<int64_t> sell_ptr((size_t)L.n_slices + 1, 0);
   for (int64_t sl = 0; sl < L.n_slices; ++sl) {
     int w = 0;
-    for (int64_t r = sl * 32; r < std::min<int64_t>(lay.off_C, sl * 32 + 32); ++r) {
+    for (int64_t p = sl * 32; p < std::min<int64_t>(lay.off_C, sl * 32 + 32); ++p) {
+      const int r = perm[p];
       HHG_CHECK(len[r] >= 0, HHG_EINVAL, "lower-primitive row wider than the assembly buffer");
       w = std::max(w, len[r]);
     }
@@ -382,6 +393,7 @@ LevelView<double> view<double>(hhg_shell* s, int n) {
   v.all_nodes = L.d_all_nodes;
   for (int cc = 0; cc < 5; ++cc) v.colour_off[cc] = L.colour_off[cc];
   v.sell_ptr = L.d_sell_ptr; v.sell_col = L.d_sell_col; v.sell_val = L.d_sell_val; v.low_diag = L.d_low_diag;
+  v.low_perm = L.d_low_perm; v.low_pos = L.d_low_pos;
   v.err = s->d_err;
   v.nrhs = s->nb;
   v.vstride = lay.n_total;
@@ -406,8 +418,9 @@ LevelView<float> view<float>(hhg_shell* s, int n) {
   v.all_nodes = d.all_nodes;
   for (int cc = 0; cc < 5; ++cc) v.colour_off[cc] = d.colour_off[cc];
   v.sell_ptr = d.sell_ptr; v.sell_col = d.sell_col; v.sell_val = L.d_sell_val32; v.low_diag = L.d_low_diag32;
+  v.low_perm = d.low_perm; v.low_pos = d.low_pos;
   v.err = d.err;
-  v.smooth_cfg = L.tune32 >= 0 ? L.tune32 : -1;
+  v.smooth_cfg = L.tune32 == TUNE_NONE ? -1 : L.tune32;
   v.nrhs = d.nrhs;
   v.vstride = d.vstride;
   v.gstride = d.gstride;
@@ -433,8 +446,8 @@ static void tune_smooth32(hhg_shell* s, cudaStream_t st) {
     v.nrhs = 1;
     float best_ms = 0.0f;
     int best = -1;
-    for (int cfg = -1; cfg < STAGE32_CONFIGS; ++cfg) {
-      L.tune32_ms[cfg + 1] = -1.0;
+    for (int cfg = -2; cfg < STAGE32_CONFIGS; ++cfg) {
+      L.tune32_ms[cfg + 2] = -1.0;
       if (cfg >= 0 && !stage32_supported(v, L.d_u32, cfg)) continue;
       v.smooth_cfg = cfg;
       launch_cell(v, HHG_OP_LSQP, SMOOTH, L.d_u32, L.d_u32, (const float*)L.d_f32, nullptr, st);
@@ -448,7 +461,7 @@ static void tune_smooth32(hhg_shell* s, cudaStream_t st) {
         HHG_CUDA(cudaEventElapsedTime(&t, e0, e1));
         ms = std::min(ms, t);
       }
-      L.tune32_ms[cfg + 1] = ms;
+      L.tune32_ms[cfg + 2] = ms;
       if (best_ms == 0.0f || ms < best_ms) {
         best_ms = ms;
         best = cfg;
@@ -514,15 +527,17 @@ struct TimedScope {
   cudaStream_t st;
   cudaEvent_t b = nullptr, e = nullptr;
   // n = level index, or -1 for classes timed on every level
+  // while a V-cycle is captured the events become event-record nodes of the
+  // graph (external record), re-recorded by every replay
   TimedScope(hhg_shell* s_, int n, int which_, cudaStream_t st_) : s(s_), which(which_), st(st_) {
     if (!s->timing || (n >= 0 && n != (int)s->levels.size() - 1)) return;
     HHG_CUDA(cudaEventCreate(&b));
     HHG_CUDA(cudaEventCreate(&e));
-    HHG_CUDA(cudaEventRecord(b, st));
+    HHG_CUDA(cudaEventRecordWithFlags(b, st, s->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
   }
   ~TimedScope() {
     if (!b) return;
-    cudaEventRecord(e, st);
+    cudaEventRecordWithFlags(e, st, s->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
     if (s->capturing) s->gtimed.emplace_back(which, b, e);  // an event-record node pair of the graph
     else s->tevents[which].push_back({b, e});
   }
@@ -541,7 +556,10 @@ static void graph_timed_accumulate(hhg_shell* s) {
   if (!s->timing) return;
   for (auto& t : s->gtimed) {
     float ms = 0;
-    HHG_CUDA(cudaEventElapsedTime(&ms, std::get<1>(t), std::get<2>(t)));
+    if (cudaEventElapsedTime(&ms, std::get<1>(t), std::get<2>(t)) != cudaSuccess) {
+      cudaGetLastError();  // timings of graph replays unavailable: the totals cover the launched cycles only
+      continue;
+    }
     s->gsum[std::get<0>(t)] += ms;
     s->gcnt[std::get<0>(t)] += 1;
   }
@@ -613,7 +631,7 @@ static void op_smooth(hhg_shell* s, int n, int op, const T* f, T* u, cudaStream_
   TimedScope all(s, -1, HHG_T_SMOOTH, st);
   LevelView<T> v = view<T>(s, n);
   Level& L = s->levels[n];
-  for (int t = 0; t < 6; ++t) launch_low_step(v, L.d_step[t], L.step_n[t], u, f, step_tmp<T>(L), st);
+  for (int t = 0; t < 6; ++t) launch_low_step(v, L.step_beg[t], L.step_n[t], u, f, step_tmp<T>(L), st);
   launch_halo(v, (const T*)u, st);
   TimedScope ts(s, n, HHG_T_CELL_SMOOTH, st);
   launch_cell(v, eff_op(s, n, op), SMOOTH, u, u, f, nullptr, st);
@@ -993,6 +1011,7 @@ hhg_status hhg_setup_shell(const hhg_shell_desc* d, void* stream, hhg_shell** ou
         A->off_C = L0.lay.off_C;
         A->nC = (int)L0.lay.nC;
         A->sell_ptr = L0.d_sell_ptr;
+        A->low_pos = L0.d_low_pos;
         A->sell_col = L0.d_sell_col;
         A->sell_val = L0.d_sell_val;
         A->low_diag = L0.d_low_diag;
@@ -1037,7 +1056,7 @@ hhg_status hhg_tuning(const hhg_shell* s, int L, int* cfg, double* ms) {
     const Level& Lv = s->levels[n];
     if (cfg) *cfg = Lv.tune32;
     if (ms)
-      for (int t = 0; t <= STAGE32_CONFIGS; ++t) ms[t] = Lv.tune32 == -2 ? -1.0 : Lv.tune32_ms[t];
+      for (int t = 0; t < 2 + STAGE32_CONFIGS; ++t) ms[t] = Lv.tune32 == TUNE_NONE ? -1.0 : Lv.tune32_ms[t];
   });
 }
 
@@ -1051,7 +1070,7 @@ hhg_status hhg_set_graphs(hhg_shell* s, int enable) {
 hhg_status hhg_set_tuning(hhg_shell* s, int L, int cfg) {
   return guarded([&] {
     const int n = level_index(s, L);
-    HHG_CHECK(cfg >= -1 && cfg < STAGE32_CONFIGS, HHG_EINVAL, "unknown smoother configuration");
+    HHG_CHECK(cfg >= -2 && cfg < STAGE32_CONFIGS, HHG_EINVAL, "unknown smoother configuration");
     s->levels[n].tune32 = cfg;
     ++s->gen;
   });

@@ -490,6 +490,103 @@ __global__ void __launch_bounds__(NODE_THREADS, 4) lsqp_node32_kernel(LevelView<
   }
 }
 
+// The same update with two nodes per thread in flight: both nodes' list
+// entries, neighbours and f are loaded before either is computed, so their
+// memory latencies overlap (same arithmetic per node as lsqp_node32_kernel).
+template <int Q, Mode MODE>
+__global__ void __launch_bounds__(NODE_THREADS, 4) lsqp_node32_x2_kernel(LevelView<float> lv,
+                                                                        const uint32_t* __restrict__ list, int n_list,
+                                                                        float* u, float* out, const float* f,
+                                                                        double* partial) {
+  constexpr int NP = (Q + 1) * (Q + 2) / 2;
+  constexpr int NPP = np_pad<Q>();
+  extern __shared__ __align__(16) float s_tab[];   // [N - 3][15][NPP]
+  const int c = blockIdx.x;
+  const int N = lv.N, np = N - 3;
+  const float* tab = lv.plane32 + (int64_t)c * np * 15 * NP;
+  for (int t = threadIdx.x; t < np * 15 * NPP; t += blockDim.x) {
+    const int e = t % NPP, pw = t / NPP;
+    s_tab[t] = e < NP ? tab[pw * NP + e] : 0.0f;
+  }
+  __syncthreads();
+  const int64_t base = lv.off_C + (int64_t)c * lv.n_int;
+  double nrm = 0.0;
+  for (int t = threadIdx.x; t < n_list; t += 2 * blockDim.x) {
+    float nbv[2][14], fv[2], uc[2];
+    int ii[2], jj[2], kk[2];
+    int64_t I[2];
+    bool ok[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int th = t + h * (int)blockDim.x;
+      ok[h] = th < n_list;
+      const uint32_t p = list[ok[h] ? th : t];
+      ii[h] = unpack_i(p);
+      jj[h] = unpack_j(p);
+      kk[h] = unpack_k(p);
+      I[h] = base + lin_interior32(ii[h], jj[h], kk[h], N);
+      if (deep_interior(ii[h], jj[h], kk[h], N)) {
+        int off[14];
+        neighbour_offsets(jj[h], kk[h], N, off);
+#pragma unroll
+        for (int w = 0; w < 14; ++w) nbv[h][w] = u[I[h] + off[w]];
+      } else {
+#pragma unroll
+        for (int w = 0; w < 14; ++w)
+          nbv[h][w] = load_pt(lv, (const float*)u, c, ii[h] + DI(w), jj[h] + DJ(w), kk[h] + DK(w));
+      }
+      fv[h] = MODE != APPLY ? f[I[h]] : 0.0f;
+      uc[h] = MODE != SMOOTH ? u[I[h]] : 0.0f;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (!ok[h]) continue;
+      const float* P = s_tab + (kk[h] - 1) * 15 * NPP;
+      const float ti = (float)ii[h], tj = (float)jj[h];
+      auto wt = [&](int w) -> float {
+        float Pw[NPP];
+#pragma unroll
+        for (int v = 0; v < NPP; v += 4) {
+          const float4 q4 = *reinterpret_cast<const float4*>(P + w * NPP + v);
+          Pw[v] = q4.x;
+          Pw[v + 1] = q4.y;
+          Pw[v + 2] = q4.z;
+          Pw[v + 3] = q4.w;
+        }
+        return eval_plane<float, Q>(Pw, ti, tj);
+      };
+      if (MODE == SMOOTH) {
+        float a0 = fv[h], a1 = 0.0f;
+#pragma unroll
+        for (int w = 0; w < 14; w += 2) {
+          a0 = fmaf(-wt(w), nbv[h][w], a0);
+          a1 = fmaf(-wt(w + 1), nbv[h][w + 1], a1);
+        }
+        u[I[h]] = (a0 + a1) / wt(MC);
+      } else {
+        float a0 = wt(MC) * uc[h], a1 = 0.0f;
+#pragma unroll
+        for (int w = 0; w < 14; w += 2) {
+          a0 = fmaf(wt(w), nbv[h][w], a0);
+          a1 = fmaf(wt(w + 1), nbv[h][w + 1], a1);
+        }
+        const float y = a0 + a1;
+        if (MODE == APPLY) {
+          out[I[h]] = y;
+        } else {
+          const float r = fmaf(-1.0f, y, fv[h]);
+          out[I[h]] = r;
+          nrm += (double)r * (double)r;
+        }
+      }
+    }
+  }
+  if (MODE == RESIDUAL) {
+    const double tot = block_sum(nrm);
+    if (threadIdx.x == 0) partial[c] = tot;
+  }
+}
+
 // FP32 surrogate for RB right-hand sides at once (weights evaluated once per
 // node from the per-plane table in shared memory).
 template <int Q, Mode MODE>
@@ -613,7 +710,7 @@ void launch_node32(const LevelView<float>& lv, const uint32_t* list, int n, floa
   HHG_CHECK(lv.plane32 != nullptr, HHG_ENOTFIT, "FP32 surrogate plane table missing");
   const size_t smem = sizeof(float) * (size_t)(lv.N - 3) * 15 * np_pad<Q>();
   if (lv.nrhs == 1) {
-    auto kern = lsqp_node32_kernel<Q, MODE>;
+    auto kern = lv.smooth_cfg == -2 ? lsqp_node32_x2_kernel<Q, MODE> : lsqp_node32_kernel<Q, MODE>;
     ensure_smem_limit((const void*)kern, smem);
     kern<<<lv.nC, NODE_THREADS, smem, st>>>(lv, list, n, u, out, f, partial);
     HHG_CUDA(cudaGetLastError());

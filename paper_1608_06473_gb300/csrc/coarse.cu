@@ -26,7 +26,8 @@ __device__ __forceinline__ double coarse_row(const CoarseOp& A, int64_t r, const
   if (r < A.off_C) {
     const double d = A.low_diag[r];
     if (d == 0.0) return 0.0;
-    const int64_t s = r >> 5, lane = r & 31;
+    const int64_t pr = A.low_pos[r];
+    const int64_t s = pr >> 5, lane = pr & 31;
     const int64_t beg = A.sell_ptr[s], width = (A.sell_ptr[s + 1] - beg) >> 5;
     double acc = d * p[r];
     for (int64_t kk = 0; kk < width; ++kk) {

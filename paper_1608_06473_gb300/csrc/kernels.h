@@ -74,8 +74,9 @@ void launch_low(const LevelView<T>& lv, Mode mode, const T* u, T* out, const T* 
                 int n_partial_blocks, cudaStream_t st);
 int low_blocks(int64_t rows);
 
+// One smoother step over the n rows at positions pbeg .. pbeg + n - 1.
 template <class T>
-void launch_low_step(const LevelView<T>& lv, const int* list, int n, T* u, const T* f, T* tmp, cudaStream_t st);
+void launch_low_step(const LevelView<T>& lv, int pbeg, int n, T* u, const T* f, T* tmp, cudaStream_t st);
 
 template <class T>
 void launch_zero_list(const int* list, int n, T* v, int nrhs, int64_t vstride, cudaStream_t st);
@@ -102,7 +103,8 @@ constexpr int CG_BLOCKS = 128;
 struct CoarseOp {                // exact operator of the N = 4 level
   int64_t n_total, off_C;
   int nC;
-  const int64_t* sell_ptr;       // lower-primitive rows (the level's sliced ELL)
+  const int64_t* sell_ptr;       // lower-primitive rows (the level's sliced ELL, step order)
+  const int* low_pos;            // position of a canonical row
   const int* sell_col;
   const double* sell_val;
   const double* low_diag;

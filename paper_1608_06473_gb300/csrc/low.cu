@@ -37,9 +37,10 @@ __global__ void halo_kernel(LevelView<T> lv, const T* __restrict__ u) {
       src >= 0 ? u[rb * lv.vstride + src] : T(0);
 }
 
+// Off-diagonal part of the lower row stored at position p.
 template <class T>
-__device__ __forceinline__ T low_row_offdiag(const LevelView<T>& lv, int64_t r, const T* __restrict__ u) {
-  const int64_t s = r >> 5, lane = r & 31;
+__device__ __forceinline__ T low_row_offdiag(const LevelView<T>& lv, int64_t p, const T* __restrict__ u) {
+  const int64_t s = p >> 5, lane = p & 31;
   const int64_t beg = lv.sell_ptr[s], width = (lv.sell_ptr[s + 1] - beg) >> 5;
   T acc = 0;
   for (int64_t kk = 0; kk < width; ++kk) {
@@ -62,10 +63,11 @@ __global__ void __launch_bounds__(LOW_THREADS) low_kernel(LevelView<T> lv, const
     partial += rb * lv.pstride;
   }
   double nrm = 0.0;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < lv.off_C; r += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < lv.off_C; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = lv.low_perm[p];
     const T d = lv.low_diag[r];
     T y = 0;
-    if (d != T(0)) y = fma(d, u[r], low_row_offdiag(lv, r, u));
+    if (d != T(0)) y = fma(d, u[r], low_row_offdiag(lv, p, u));
     if (MODE == APPLY) {
       out[r] = y;
     } else {
@@ -83,16 +85,16 @@ __global__ void __launch_bounds__(LOW_THREADS) low_kernel(LevelView<T> lv, const
 // One lower-primitive colour step: new values of every listed node from the
 // values at the start of the step (Eq. 5.1), written to tmp.
 template <class T>
-__global__ void low_step_kernel(LevelView<T> lv, const int* __restrict__ list, int n, const T* __restrict__ u,
-                                const T* __restrict__ f, T* __restrict__ tmp) {
+__global__ void low_step_kernel(LevelView<T> lv, int pbeg, int n, const T* __restrict__ u, const T* __restrict__ f,
+                                T* __restrict__ tmp) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const int64_t rb = blockIdx.y;
   u += rb * lv.vstride;
   f += rb * lv.vstride;
   tmp += rb * lv.tstride;
-  const int r = list[t];
-  tmp[t] = (f[r] - low_row_offdiag(lv, r, u)) / lv.low_diag[r];
+  const int r = lv.low_perm[pbeg + t];
+  tmp[t] = (f[r] - low_row_offdiag(lv, pbeg + t, u)) / lv.low_diag[r];
 }
 
 template <class T>
@@ -193,7 +195,8 @@ __global__ void restrict_low_kernel(LevelView<T> fine, LevelView<T> coarse, cons
   rc += blockIdx.y * coarse.vstride;
   const int fi = clf[r];
   if (fi < 0) { rc[r] = T(0); return; }
-  const int64_t s = (int64_t)fi >> 5, lane = fi & 31;
+  const int64_t pf = fine.low_pos[fi];
+  const int64_t s = pf >> 5, lane = pf & 31;
   const int64_t beg = fine.sell_ptr[s], width = (fine.sell_ptr[s + 1] - beg) >> 5;
   T acc = 0;
   for (int64_t kk = 0; kk < width; ++kk) {
@@ -298,7 +301,8 @@ __global__ void low_assemble_kernel(LevelView<double> lv, int pass, const int64_
     return;
   }
   diag[r] = dsum;
-  const int64_t sl = r >> 5, lane = r & 31;
+  const int64_t pr = lv.low_pos[r];
+  const int64_t sl = pr >> 5, lane = pr & 31;
   const int64_t sb = sell_ptr[sl], width = (sell_ptr[sl + 1] - sb) >> 5;
   for (int64_t kk = 0; kk < width; ++kk) {
     const int64_t e = sb + kk * 32 + lane;
@@ -333,11 +337,11 @@ void launch_low(const LevelView<T>& lv, Mode mode, const T* u, T* out, const T* 
 }
 
 template <class T>
-void launch_low_step(const LevelView<T>& lv, const int* list, int n, T* u, const T* f, T* tmp, cudaStream_t st) {
+void launch_low_step(const LevelView<T>& lv, int pbeg, int n, T* u, const T* f, T* tmp, cudaStream_t st) {
   if (n == 0) return;
   const dim3 g(grid_for(n, 256), lv.nrhs);
-  low_step_kernel<T><<<g, 256, 0, st>>>(lv, list, n, u, f, tmp);
-  scatter_kernel<T><<<g, 256, 0, st>>>(list, n, tmp, u, lv.tstride, lv.vstride);
+  low_step_kernel<T><<<g, 256, 0, st>>>(lv, pbeg, n, u, f, tmp);
+  scatter_kernel<T><<<g, 256, 0, st>>>(lv.low_perm + pbeg, n, tmp, u, lv.tstride, lv.vstride);
   HHG_CUDA(cudaGetLastError());
   count_launch(2);
 }
@@ -404,7 +408,7 @@ void launch_low_assemble(const LevelView<double>& lv, int pass, const int64_t* i
 #define INST(T)                                                                                                   \
   template void launch_halo<T>(const LevelView<T>&, const T*, cudaStream_t);                                      \
   template void launch_low<T>(const LevelView<T>&, Mode, const T*, T*, const T*, double*, int, cudaStream_t);    \
-  template void launch_low_step<T>(const LevelView<T>&, const int*, int, T*, const T*, T*, cudaStream_t);        \
+  template void launch_low_step<T>(const LevelView<T>&, int, int, T*, const T*, T*, cudaStream_t);               \
   template void launch_zero_list<T>(const int*, int, T*, int, int64_t, cudaStream_t);                             \
   template void launch_prolong_add<T>(const LevelView<T>&, const LevelView<T>&, const int*, const T*, T*,         \
                                       cudaStream_t);                                                              \

@@ -13,6 +13,7 @@
 namespace hhg {
 
 constexpr int STAGE32_CONFIGS_MAX = 4;  // staged FP32 smoother configurations (stage.cu)
+constexpr int TUNE_NONE = -9;           // FP32 smoother of a level not tuned yet
 
 // Geometry of one macro cell: its 4 vertices (ascending global id) and the
 // radii that rho interpolates (Sec. 2.2, blending map Phi).
@@ -71,12 +72,16 @@ struct LevelView {
   int colour_off[5];             // start of each colour in colour_nodes
   // lower primitives: canonical rows 0 .. off_C-1 in sliced ELL (32-row
   // slices, column-major inside a slice), Dirichlet rows have diag 0
+  // rows stored in smoother-step order: position p holds canonical row
+  // low_perm[p], canonical row r sits at position low_pos[r]; slice p >> 5
   const int64_t* sell_ptr;       // [n_slices + 1]
   const int* sell_col;           // canonical column, -1 = padding
   const T* sell_val;
+  const int* low_perm;           // [off_C]
+  const int* low_pos;            // [off_C]
   const T* low_diag;             // [off_C]
   int* err;                      // device error word: set to 1 when a bounded wait gives up
-  int smooth_cfg;                // FP32 surrogate smoother: -1 = per-colour node kernel, else staged configuration
+  int smooth_cfg;                // FP32 surrogate smoother: -1 / -2 = per-colour node kernel (1 / 2 nodes per thread in flight), >= 0 = staged
   // right-hand sides processed together: vector b of a level lives at
   // v + b vstride, its halo copy at ghost + b gstride, its residual partials
   // at partial + b pstride, its lower-step buffer at tmp + b tstride
@@ -107,7 +112,9 @@ struct Level {
   double* d_low_diag = nullptr;
   float* d_sell_val32 = nullptr;
   float* d_low_diag32 = nullptr;
-  int* d_step[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int* d_low_perm = nullptr;      // lower rows in step order (see LevelView)
+  int* d_low_pos = nullptr;
+  int step_beg[6] = {0, 0, 0, 0, 0, 0};   // first position of each smoother step
   int step_n[6] = {0, 0, 0, 0, 0, 0};
   int max_step = 0;
   int* d_dirichlet = nullptr;    // Dirichlet lower nodes
@@ -126,10 +133,11 @@ struct Level {
   uint32_t* d_colour_nodes = nullptr;
   uint32_t* d_all_nodes = nullptr;
   int colour_off[5] = {0, 0, 0, 0, 0};
-  // FP32 surrogate smoother chosen by the tuner (-2 = not tuned, -1 = per-colour
-  // node kernel, >= 0 = staged configuration) and the candidates' times (ms)
-  int tune32 = -2;
-  double tune32_ms[1 + STAGE32_CONFIGS_MAX] = {};
+  // FP32 surrogate smoother chosen by the tuner (TUNE_NONE = not tuned, -1 =
+  // per-colour node kernel, -2 = the same with two nodes per thread in flight,
+  // >= 0 = staged configuration) and the candidates' times (ms; index cfg + 2)
+  int tune32 = TUNE_NONE;
+  double tune32_ms[2 + STAGE32_CONFIGS_MAX] = {};
   // halo copies and work vectors (allocated on demand)
   double* d_ghost64 = nullptr;
   float* d_ghost32 = nullptr;
