@@ -66,7 +66,7 @@ def parse():
     p.add_argument("--j", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--mode", choices=["solve", "smoother", "serve"], default="solve",
+    p.add_argument("--mode", choices=["solve", "smoother", "serve", "variants"], default="solve",
                    help="solve: the whole path per step (default); smoother: finest-level sweeps only "
                         "(for profiling the smoother kernels)")
     p.add_argument("--op", choices=["lsqp", "ifem"], default="lsqp", help="operator for --mode smoother")
@@ -466,6 +466,53 @@ def serve_run(n_requests, rate_hz=200.0, seed=2024, max_inflight=4, warm=True):
                         "resident (built before the stream)" % rate_hz}
 
 
+def run_variants(args):
+    """V(3,3) solves to 1e-8 of the method variants on the workload (FP64):
+    LSQP q = 1, 2, 3 (j = 2), IPOLY, IFEM, and double discretisation (LSQP
+    smoothing, IFEM residuals, stopped on the updates).  Per variant: the fit
+    time, the solve time (CUDA events), cycles and the mean convergence
+    factor."""
+    import torch
+
+    import paper_1608_06473_gb300 as hhg
+    import synthetic
+    tang, layers, L, desc = WORKLOADS[args.workload]
+    stream = torch.cuda.current_stream()
+    s = hhg.Shell(0.55, 1.0, tang, layers, L, stream=stream)
+    n_total, n_free = s.num_nodes()
+    f = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_F)).cuda()
+    u = torch.zeros_like(f)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    out = {}
+    plan = [("lsqp_q1", hhg.HHG_OP_LSQP, ("lsqp", 1)), ("lsqp_q2", hhg.HHG_OP_LSQP, ("lsqp", 2)),
+            ("lsqp_q3", hhg.HHG_OP_LSQP, ("lsqp", 3)), ("ipoly", hhg.HHG_OP_LSQP, ("ipoly", 2)),
+            ("dd_lsqp_q2", hhg.HHG_OP_DD, ("lsqp", 2)), ("ifem", hhg.HHG_OP_IFEM, None)]
+    s.fit(2, 2, stream=stream)
+    s.vcycle(f, u, max_cycles=2, rtol=0.0, stream=stream, raise_on_noconv=False)   # warm-up
+    for name, op, fit in plan:
+        a, b = ev(), ev()
+        a.record(stream)
+        if fit and fit[0] == "lsqp":
+            s.fit(fit[1], 2, stream=stream)
+        elif fit:
+            s.fit_ipoly(stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_fit = a.elapsed_time(b) * 1e-3
+        u.zero_()
+        a.record(stream)
+        rel, cycles, st = s.vcycle(f, u, max_cycles=60, rtol=1e-8, op=op, stream=stream, raise_on_noconv=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        sec = a.elapsed_time(b) * 1e-3
+        out[name] = {"fit_s": t_fit, "solve_s": sec, "cycles": cycles, "relres": float(rel[0]),
+                     "rate": float(rel[0]) ** (1.0 / max(cycles, 1)),
+                     "stop": "updates" if op == hhg.HHG_OP_DD else "residual"}
+    s.close()
+    return {"mode": "variants", "workload": args.workload, "shell": desc, "unknowns": n_free, "cycle": "V(3,3)",
+            "rtol": 1e-8, "variants": out}
+
+
 def run_smoother(args):
     """Finest-level smoother only: setup, fit, `warmup` sweeps, then `steps`
     sweeps timed with CUDA events on the launching stream."""
@@ -510,6 +557,9 @@ def main():
         return
     if args.mode == "serve":
         print(json.dumps(serve_run(args.serve_requests)))
+        return
+    if args.mode == "variants":
+        print(json.dumps(run_variants(args)))
         return
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))

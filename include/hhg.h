@@ -78,7 +78,10 @@ typedef enum {
 
 typedef enum {
   HHG_OP_IFEM = 0,     /* exact stencils, assembled on the fly (Sec. 4.2.1) */
-  HHG_OP_LSQP = 1      /* least-squares surrogate stencils (Sec. 3.2) */
+  HHG_OP_LSQP = 1,     /* the fitted surrogate stencils: LSQP (Sec. 3.2) or IPOLY (Sec. 3.1) */
+  HHG_OP_DD = 2        /* double discretisation (Sec. 4.1): relaxation with the
+                          fitted surrogate, residuals and apply with the exact
+                          stencils; hhg_vcycle stops on the updates */
 } hhg_op;
 
 /* Arithmetic of a call.  hhg_apply / hhg_residual / hhg_smooth: the vectors
@@ -132,6 +135,14 @@ hhg_status hhg_node_coords(const hhg_shell* shell, int L, double* xyz_host);
  * stencil (Sec. 3, first paragraph).  May be called again to refit. */
 hhg_status hhg_fit_surrogate(hhg_shell* shell, int q, int j, void* stream);
 
+/* IPOLY setup (Sec. 3.1): the quadratic (q = 2) polynomials interpolating the
+ * exact stencils at ten points of every macro cell and level L >= 3 -- the
+ * quadratic nodes of the cell shrunk to its interior, (1,1,1), (1,1,a),
+ * (1,a,1), (a,1,1), (1,1,b), (1,b,1), (b,1,1), (1,b,b), (b,1,b), (b,b,1) with
+ * a = N - 3, b = N/2 - 1.  Replaces any previous fit; HHG_OP_LSQP and
+ * HHG_OP_DD then use these polynomials. */
+hhg_status hhg_fit_ipoly(hhg_shell* shell, void* stream);
+
 /* y = L_L u (op = IFEM) or y = L~_L u (op = LSQP) on level L, for nrhs
  * vectors (Sec. 3.4, the operator of Eq. 3.4).  u and y must not overlap. */
 hhg_status hhg_apply(hhg_shell* shell, int L, hhg_op op, hhg_dtype dtype,
@@ -160,7 +171,11 @@ hhg_status hhg_smooth(hhg_shell* shell, int L, hhg_op op, hhg_dtype dtype,
  * iterate; cycles stop once ||f - L u||_2 <= rtol ||f - L u_0||_2 for every
  * right-hand side or after max_cycles (HHG_ENOCONV).  relres_out (nullable,
  * nrhs) receives the final relative residuals, cycles_out (nullable) the
- * number of cycles run. */
+ * number of cycles run.  op = HHG_OP_DD (double discretisation, Sec. 4.1):
+ * smoothing with the surrogate, residuals with the exact stencils, and the
+ * stopping test on the updates instead of the residual,
+ * ||u_k - u_{k-1}||_2 <= rtol ||u_1 - u_0||_2, as that section recommends;
+ * relres_out then holds that ratio. */
 hhg_status hhg_vcycle(hhg_shell* shell, hhg_op op, hhg_dtype dtype,
                       const void* f, void* u, int nu1, int nu2, int max_cycles,
                       double rtol, int nrhs, double* relres_out, int* cycles_out,

@@ -91,6 +91,20 @@ def fit(level: M.Level, A: sp.csr_matrix, q: int = 2, j: int = 2, cells=None) ->
     return out
 
 
+def fit_ipoly(level: M.Level, A: sp.csr_matrix, cells=None) -> np.ndarray:
+    """IPOLY (Sec. 3.1): the quadratic polynomials interpolating the exact
+    off-centre weights at the ten points of ipoly_points (a square system,
+    solved like the least-squares one); shape (n_cells, 14, 10)."""
+    N = level.N
+    assert level_index(N) >= 1
+    pts = ipoly_points(N)
+    cells = np.arange(level.shell.nC) if cells is None else np.asarray(cells)
+    out = np.empty((len(cells), 14, n_coeffs(2)))
+    for n, c in enumerate(cells):
+        out[n] = fit_values(pts, N, 2, exact_weights_at(level, A, c, pts)[:, :14])
+    return out
+
+
 def fit_values(pts: np.ndarray, N: int, q: int, b: np.ndarray) -> np.ndarray:
     """argmin_z ||A z - b||_2 (Sec. 3.2) for every column of b (values at the
     sampling points), by Householder QR; returns (n_columns, m_q)."""

@@ -185,27 +185,51 @@ class CoarseSolver:
 
 class Hierarchy:
     """Operators on levels N = 4, 8, ..., N_fine and the transfers between
-    them.  ops[0] is the coarsest (N = 4)."""
+    them.  ops[0] is the coarsest (N = 4).  smooth_ops (optional, same
+    levels) are the operators of the relaxation sweeps; by default the
+    sweeps use ops.  Double discretisation (Sec. 4.1, "DD") relaxes with the
+    surrogate and computes residuals with the exact operator: smooth_ops =
+    surrogate operators, ops = exact ones."""
 
-    def __init__(self, levels, ops):
+    def __init__(self, levels, ops, smooth_ops=None):
         self.levels = levels
         self.ops = ops
+        self.smooth_ops = ops if smooth_ops is None else smooth_ops
         self.transfers = [Transfer(levels[n + 1], levels[n]) for n in range(len(levels) - 1)]
         self.coarse = CoarseSolver(ops[0])
 
     def vcycle(self, n, u, f, nu1=3, nu2=3):
-        op = self.ops[n]
+        op, sm = self.ops[n], self.smooth_ops[n]
         if n == 0:
             return self.coarse.solve(f)
         for _ in range(nu1):
-            u = op.sweep(u, f)
+            u = sm.sweep(u, f)
         r = op.residual(u, f)
         tr = self.transfers[n - 1]
         e = self.vcycle(n - 1, np.zeros(self.levels[n - 1].n_total), tr.restrict(r), nu1, nu2)
         u = u + tr.prolong(e)
         for _ in range(nu2):
-            u = op.sweep(u, f)
+            u = sm.sweep(u, f)
         return u
+
+    def solve_updates(self, f, u0=None, nu1=3, nu2=3, rtol=1e-8, max_cycles=50):
+        """V-cycles stopped on the updates instead of the residual (the
+        stopping rule Sec. 4.1 recommends for double discretisation): stop
+        once ||u_k - u_{k-1}||_2 <= rtol ||u_1 - u_0||_2 (free nodes).
+        Returns u and the history of relative update norms (entry 0 is 1)."""
+        n = len(self.ops) - 1
+        op = self.ops[n]
+        u = np.zeros(self.levels[n].n_total) if u0 is None else op.mask * u0
+        hist, d0 = [], None
+        for _ in range(max_cycles):
+            un = self.vcycle(n, u, f, nu1, nu2)
+            d = np.linalg.norm((un - u)[self.levels[n].free])
+            u = un
+            d0 = d if d0 is None else d0
+            hist.append(d / d0 if d0 > 0 else 0.0)
+            if hist[-1] <= rtol:
+                break
+        return u, hist
 
     def solve(self, f, u0=None, nu1=3, nu2=3, rtol=1e-8, max_cycles=50):
         """V(nu1, nu2) cycles on the finest level; returns u and the history of
@@ -224,18 +248,23 @@ class Hierarchy:
 
 
 def build_hierarchy(shell: M.Shell, N_fine: int, op: str = "lsqp", q: int = 2, j: int = 2):
-    """Levels, operators (exact 'ifem' or surrogate 'lsqp' on N >= 8) and
-    transfers for a shell."""
+    """Levels, operators and transfers for a shell: op = 'ifem' (exact),
+    'lsqp' or 'ipoly' (surrogate on N >= 8), or 'dd-lsqp' / 'dd-ipoly'
+    (double discretisation: surrogate sweeps, exact residuals)."""
     from . import fem as F
     from . import lsqp as LS
-    levels, ops = [], []
+    levels, ops, sms = [], [], []
     N = 4
     while N <= N_fine:
         lv = M.make_level(shell, N)
         A = F.assemble(lv)
-        if op == "lsqp" and N >= 8:
-            A = LS.surrogate_operator(lv, A, LS.fit(lv, A, q, j), q)
+        S = A
+        kind = op.split("-")[-1]
+        if kind in ("lsqp", "ipoly") and N >= 8:
+            coef = LS.fit(lv, A, q, j) if kind == "lsqp" else LS.fit_ipoly(lv, A)
+            S = LS.surrogate_operator(lv, A, coef, q if kind == "lsqp" else 2)
         levels.append(lv)
-        ops.append(Operator(lv, A))
+        ops.append(Operator(lv, A if op.startswith("dd-") else S))
+        sms.append(Operator(lv, S))
         N *= 2
-    return Hierarchy(levels, ops)
+    return Hierarchy(levels, ops, sms if op.startswith("dd-") else None)

@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "libhhg.so")
 
 HHG_OK, HHG_EINVAL, HHG_ENOMEM, HHG_ECUDA, HHG_ENOTFIT, HHG_ENOCONV, HHG_EDIVERGED, HHG_ETIMEOUT = \
     0, -1, -2, -3, -4, -5, -6, -7
-HHG_OP_IFEM, HHG_OP_LSQP = 0, 1
+HHG_OP_IFEM, HHG_OP_LSQP, HHG_OP_DD = 0, 1, 2
 HHG_F64, HHG_F32 = 0, 1
 
 
@@ -78,6 +78,7 @@ _SIGS = {
     "hhg_num_nodes": [_P, _I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "hhg_node_coords": [_P, _I, _P],
     "hhg_fit_surrogate": [_P, _I, _I, _P],
+    "hhg_fit_ipoly": [_P, _P],
     "hhg_apply": [_P, _I, _I, _I, _P, _P, _I, _P],
     "hhg_residual": [_P, _I, _I, _I, _P, _P, _P, _I, _P, _P],
     "hhg_smooth": [_P, _I, _I, _I, _P, _P, _I, _I, _P],
@@ -228,6 +229,10 @@ def hhg_fit_surrogate(shell: int, q: int = 2, j: int = 2, stream=None):
     _check(lib().hhg_fit_surrogate(shell, q, j, _stream(stream)))
 
 
+def hhg_fit_ipoly(shell: int, stream=None):
+    _check(lib().hhg_fit_ipoly(shell, _stream(stream)))
+
+
 def hhg_apply(shell: int, L: int, op: int, dtype: int, u, y, nrhs: int = 1, stream=None):
     _check(lib().hhg_apply(shell, L, op, dtype, _ptr(u), _ptr(y), nrhs, _stream(stream)))
 
@@ -299,6 +304,9 @@ class Shell:
 
     def fit(self, q=2, j=2, stream=None):
         hhg_fit_surrogate(self.handle, q, j, stream)
+
+    def fit_ipoly(self, stream=None):
+        hhg_fit_ipoly(self.handle, stream)
 
     def apply(self, u, y, L=None, op=HHG_OP_LSQP, dtype=HHG_F64, nrhs=1, stream=None):
         hhg_apply(self.handle, self.L if L is None else L, op, dtype, u, y, nrhs, stream)

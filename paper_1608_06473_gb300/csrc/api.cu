@@ -586,11 +586,16 @@ static void timing_clear(hhg_shell* s) {
 // ---------------------------------------------------------------------------
 
 static void check_op(hhg_shell* s, int n, int op) {
-  HHG_CHECK(op == HHG_OP_IFEM || op == HHG_OP_LSQP, HHG_EINVAL, "unknown operator");
-  if (op == HHG_OP_LSQP && s->levels[n].N >= 8)
+  HHG_CHECK(op == HHG_OP_IFEM || op == HHG_OP_LSQP || op == HHG_OP_DD, HHG_EINVAL, "unknown operator");
+  if (op != HHG_OP_IFEM && s->levels[n].N >= 8)
     HHG_CHECK(s->levels[n].d_coef != nullptr, HHG_ENOTFIT, "LSQP requested before hhg_fit_surrogate");
 }
 
+// Kernels of an operator choice: double discretisation (Sec. 4.1) relaxes
+// with the fitted surrogate and computes residuals (and applies) with the
+// exact stencils.
+static int smooth_op(int op) { return op == HHG_OP_DD ? HHG_OP_LSQP : op; }
+static int exact_op(int op) { return op == HHG_OP_DD ? HHG_OP_IFEM : op; }
 static int eff_op(hhg_shell* s, int n, int op) { return (s->levels[n].N >= 8) ? op : HHG_OP_IFEM; }
 
 template <class T = double>
@@ -599,7 +604,7 @@ static void op_apply(hhg_shell* s, int n, int op, const T* u, T* y, cudaStream_t
   launch_halo(v, u, st);
   {
     TimedScope ts(s, n, HHG_T_CELL_APPLY, st);
-    launch_cell(v, eff_op(s, n, op), APPLY, const_cast<T*>(u), y, (const T*)nullptr, nullptr, st);
+    launch_cell(v, eff_op(s, n, exact_op(op)), APPLY, const_cast<T*>(u), y, (const T*)nullptr, nullptr, st);
   }
   launch_low(v, APPLY, u, y, (const T*)nullptr, nullptr, low_blocks(v.off_C), st);
 }
@@ -620,7 +625,7 @@ static void op_residual(hhg_shell* s, int n, int op, const T* u, const T* f, T* 
   launch_halo(v, u, st);
   {
     TimedScope ts(s, n, HHG_T_CELL_RESIDUAL, st);
-    launch_cell(v, eff_op(s, n, op), RESIDUAL, const_cast<T*>(u), r, f, part, st);
+    launch_cell(v, eff_op(s, n, exact_op(op)), RESIDUAL, const_cast<T*>(u), r, f, part, st);
   }
   launch_low(v, RESIDUAL, u, r, f, part + v.nC, nb, st);
   launch_sum(part, v.nC + nb, v.nrhs, v.pstride, scal(s, slot), st);
@@ -634,7 +639,7 @@ static void op_smooth(hhg_shell* s, int n, int op, const T* f, T* u, cudaStream_
   for (int t = 0; t < 6; ++t) launch_low_step(v, L.step_beg[t], L.step_n[t], u, f, step_tmp<T>(L), st);
   launch_halo(v, (const T*)u, st);
   TimedScope ts(s, n, HHG_T_CELL_SMOOTH, st);
-  launch_cell(v, eff_op(s, n, op), SMOOTH, u, u, f, nullptr, st);
+  launch_cell(v, eff_op(s, n, smooth_op(op)), SMOOTH, u, u, f, nullptr, st);
 }
 
 // Reports (and clears) a bounded device-side wait that gave up since the
@@ -771,7 +776,11 @@ static void vcycle_rec32(hhg_shell* s, int n, int op, const float* f, float* u, 
 // surrogate fit
 // ---------------------------------------------------------------------------
 
-static void fit(hhg_shell* s, int q, int j, cudaStream_t st) {
+// ipoly = false: LSQP on S_l = M_{m(l,j)} (Sec. 3.2); ipoly = true: IPOLY
+// (Sec. 3.1), q = 2 interpolation at the ten quadratic nodes of the macro
+// cell shrunk to its interior, a = N - 3, b = N/2 - 1 (the square system is
+// solved by the same QR).
+static void fit(hhg_shell* s, int q, int j, cudaStream_t st, bool ipoly = false) {
   TimedScope all(s, -1, HHG_T_FIT, st);
   const int mq = n_coeffs(q);
   for (size_t n = 0; n < s->levels.size(); ++n) {
@@ -779,12 +788,19 @@ static void fit(hhg_shell* s, int q, int j, cudaStream_t st) {
     const int N = L.N;
     if (N < 8) continue;
     const int l = (int)n;  // paper level: N = 2^(l+2)
-    const int mlev = std::min(l, std::max(1, j));
-    const int Nm = 4 << mlev, scale = 1 << (l - mlev);
     std::vector<uint32_t> pts;
-    for (int k = 1; k < Nm; ++k)
-      for (int jj = 1; jj < Nm - k; ++jj)
-        for (int i = 1; i < Nm - jj - k; ++i) pts.push_back(pack_ijk(i * scale, jj * scale, k * scale));
+    if (ipoly) {
+      const int a = N - 3, b = N / 2 - 1;
+      const int P[10][3] = {{1, 1, 1}, {1, 1, a}, {1, a, 1}, {a, 1, 1}, {1, 1, b},
+                            {1, b, 1}, {b, 1, 1}, {1, b, b}, {b, 1, b}, {b, b, 1}};
+      for (auto& p : P) pts.push_back(pack_ijk(p[0], p[1], p[2]));
+    } else {
+      const int mlev = std::min(l, std::max(1, j));
+      const int Nm = 4 << mlev, scale = 1 << (l - mlev);
+      for (int k = 1; k < Nm; ++k)
+        for (int jj = 1; jj < Nm - k; ++jj)
+          for (int i = 1; i < Nm - jj - k; ++i) pts.push_back(pack_ijk(i * scale, jj * scale, k * scale));
+    }
     const int np = (int)pts.size();
     // sampling matrix in the line-form monomial order (a, d, b): xi^a eta^b zeta^d
     std::vector<double> Am((size_t)np * mq), sc(mq);
@@ -841,7 +857,7 @@ static void fit(hhg_shell* s, int q, int j, cudaStream_t st) {
     A.release(d_sc);
   }
   s->q = q;
-  s->j = j;
+  s->j = ipoly ? 0 : j;
   ++s->gen;
   s->cg_graph_iters = 0;
   tune_smooth32(s, st);
@@ -1041,6 +1057,7 @@ hhg_status hhg_destroy(hhg_shell* s) {
     timing_clear(s);
     if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
     graph_timed_clear(s);
+    s->d_uprev = nullptr;
     if (s->gstream) cudaStreamDestroy(s->gstream);
     for (cudaEvent_t e : s->gev)
       if (e) cudaEventDestroy(e);
@@ -1089,6 +1106,13 @@ hhg_status hhg_node_coords(const hhg_shell* s, int L, double* xyz) {
     const int n = level_index(const_cast<hhg_shell*>(s), L);
     HHG_CHECK(xyz != nullptr, HHG_EINVAL, "NULL output");
     level_coords(s->mesh, s->levels[n].lay, xyz);
+  });
+}
+
+hhg_status hhg_fit_ipoly(hhg_shell* s, void* stream) {
+  return guarded([&] {
+    HHG_CHECK(s != nullptr, HHG_EINVAL, "NULL shell");
+    fit(s, 2, 0, (cudaStream_t)stream, true);
   });
 }
 
@@ -1287,9 +1311,22 @@ static int solve_batch(hhg_shell* s, int op, int dtype, const double* f, double*
   const int n = (int)s->levels.size() - 1, nb = s->nb;
   Level& Lv = s->levels[n];
   const int64_t nt = Lv.lay.n_total;
+  const bool dd = op == HHG_OP_DD;
+  double* uprev = nullptr;
+  if (dd) {  // double discretisation stops on the updates u_k - u_{k-1} (Sec. 4.1)
+    if (s->uprev_len < nt * s->cap) {
+      s->alloc.release(s->d_uprev);
+      s->d_uprev = nullptr;
+      s->d_uprev = s->alloc.alloc_n<double>((size_t)(nt * s->cap));
+      s->uprev_len = nt * s->cap;
+      ++s->gen;
+    }
+    uprev = s->d_uprev;
+  }
   launch_zero_list(Lv.d_dirichlet, Lv.n_dirichlet, u, nb, nt, st);
   op_residual(s, n, op, u, f, Lv.d_r, 10, st);
   std::vector<double> r0 = read_scalars(s, 10, st);
+  std::vector<double> d0((size_t)nb, -1.0);
   bool todo = false;
   for (int b = 0; b < nb; ++b) {
     r0[b] = std::sqrt(r0[b]);
@@ -1299,6 +1336,7 @@ static int solve_batch(hhg_shell* s, int op, int dtype, const double* f, double*
   }
   if (dtype == HHG_F32) ensure_f32(s, st);
   auto cycle = [&](cudaStream_t cs) {
+    if (dd) HHG_CUDA(cudaMemcpyAsync(uprev, u, sizeof(double) * nt * nb, cudaMemcpyDeviceToDevice, cs));
     if (dtype == HHG_F32) {
       // iterative refinement: e = one FP32 V-cycle on L e = r (e0 = 0), u += e
       launch_copy_cast<float>(Lv.d_r, Lv.d_f32, nt * nb, cs);
@@ -1357,7 +1395,11 @@ static int solve_batch(hhg_shell* s, int op, int dtype, const double* f, double*
       HHG_CUDA(cudaEventRecord(s->gev[1], s->gstream));
       HHG_CUDA(cudaStreamWaitEvent(st, s->gev[1], 0));
     }
-    op_residual(s, n, op, u, f, Lv.d_r, 10, st);
+    if (dd) {
+      launch_diff_norm(u, uprev, nt, nb, parts(s), s->pstride, scal(s, 10), st);
+    } else {
+      op_residual(s, n, op, u, f, Lv.d_r, 10, st);
+    }
     const std::vector<double> rn = read_scalars(s, 10, st);
     if (graphs && cyc > 0) graph_timed_accumulate(s);
     check_device_error(s, st);
@@ -1365,7 +1407,12 @@ static int solve_batch(hhg_shell* s, int op, int dtype, const double* f, double*
     for (int b = 0; b < nb; ++b) {
       const double v = std::sqrt(rn[b]);
       HHG_CHECK(std::isfinite(v), HHG_EDIVERGED, "residual norm became NaN or Inf");
-      rel[b] = r0[b] > 0 ? v / r0[b] : 0.0;
+      if (dd) {
+        if (d0[b] < 0) d0[b] = v;  // the first update
+        rel[b] = d0[b] > 0 ? v / d0[b] : 0.0;
+      } else {
+        rel[b] = r0[b] > 0 ? v / r0[b] : 0.0;
+      }
       todo = todo || rel[b] > rtol;
     }
     ++cyc;
@@ -1460,7 +1507,7 @@ extern "C" hhg_status hhg_residual_noalloc(hhg_shell* s, int L, hhg_op op, const
     double* part = noalloc_scratch();
     cudaStream_t st = (cudaStream_t)stream;
     launch_halo(v, u, st);
-    launch_cell(v, eff_op(s, n, op), RESIDUAL, const_cast<double*>(u), r, f, part, st);
+    launch_cell(v, eff_op(s, n, exact_op(op)), RESIDUAL, const_cast<double*>(u), r, f, part, st);
     launch_low(v, RESIDUAL, u, r, f, part + v.nC, nb, st);
     launch_sum(part, v.nC + nb, 1, 0, norm2_dev, st);
   });

@@ -89,6 +89,10 @@ template <class T>
 void launch_restrict(const LevelView<T>& fine, const LevelView<T>& coarse, const int* coarse_low_fine,
                      const T* rf, T* rc, cudaStream_t st);
 
+// out[b] = ||a_b - b_b||^2 over n entries per right-hand side (vectors n
+// apart), through partial (pstride per right-hand side, fixed order).
+void launch_diff_norm(const double* a, const double* b, int64_t n, int nrhs, double* partial, int pstride,
+                      double* out, cudaStream_t st);
 // out[b] = sum of partial[b pstride .. b pstride + n - 1], b < nrhs (fixed
 // order, one block per right-hand side).
 void launch_sum(const double* partial, int n, int nrhs, int pstride, double* out, cudaStream_t st);

@@ -7,6 +7,8 @@
 // values the paper reassembles on the fly, Sec. 2.3) and stored as sliced
 // ELL rows over canonical columns.  Their O(2^{2l}) nodes (Sec. 2.3) are a
 // small share of the work.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -215,6 +217,21 @@ __global__ void sum_kernel(const double* __restrict__ partial, int n, int pstrid
   if (threadIdx.x == 0) out[blockIdx.x] = v;
 }
 
+// Partial sums of ||a_b - b_b||^2 per block and right-hand side (grid y).
+__global__ void diff_norm_kernel(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+                                 double* partial, int pstride) {
+  const int64_t rb = blockIdx.y;
+  a += rb * n;
+  b += rb * n;
+  double v = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const double d = a[t] - b[t];
+    v = fma(d, d, v);
+  }
+  v = block_sum(v);
+  if (threadIdx.x == 0) partial[rb * pstride + blockIdx.x] = v;
+}
+
 template <class T>
 __global__ void copy_cast_kernel(const double* __restrict__ src, T* __restrict__ dst, int64_t n) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -373,6 +390,15 @@ void launch_restrict(const LevelView<T>& fine, const LevelView<T>& coarse, const
   restrict_low_kernel<T><<<dim3(grid_for(coarse.off_C, 256), fine.nrhs), 256, 0, st>>>(fine, coarse, clf, rf, rc);
   HHG_CUDA(cudaGetLastError());
   count_launch(n ? 2 : 1);
+}
+
+void launch_diff_norm(const double* a, const double* b, int64_t n, int nrhs, double* partial, int pstride,
+                      double* out, cudaStream_t st) {
+  const int nblk = std::min(pstride, 1024);
+  diff_norm_kernel<<<dim3(nblk, nrhs), 256, 0, st>>>(a, b, n, partial, pstride);
+  HHG_CUDA(cudaGetLastError());
+  count_launch();
+  launch_sum(partial, nblk, nrhs, pstride, out, st);
 }
 
 void launch_sum(const double* partial, int n, int nrhs, int pstride, double* out, cudaStream_t st) {

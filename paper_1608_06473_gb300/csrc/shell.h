@@ -175,6 +175,8 @@ struct hhg_shell {
   double* d_red = nullptr;             // reduction scratch (partials + results)
   int64_t red_len = 0;
   double* d_cg = nullptr;              // coarse-solver vectors
+  double* d_uprev = nullptr;           // previous iterate of double-discretisation cycles
+  int64_t uprev_len = 0;
   int* d_err = nullptr;                // device error word of the staged kernels (0 = ok)
   // batches: work vectors, halo copies, step buffers, reduction and coarse
   // solver scratch hold `cap` right-hand sides; `nb` of them are active in
