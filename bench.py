@@ -168,9 +168,9 @@ class ClockSampler:
 
 def traffic_record(kernel: str, workload: str):
     """ncu DRAM bytes per launch of `kernel` on `workload`, if recorded for the
-    current kernel source (profiles/traffic.json, written from an ncu capture);
+    current kernel source (profiles/traffic.txt, JSON written from an ncu capture);
     None when absent or when the source changed since the capture."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path)).get(f"{kernel}@{workload}")
