@@ -116,6 +116,22 @@ typedef struct {
  * Work is enqueued on `stream` and completed before return. */
 hhg_status hhg_setup_shell(const hhg_shell_desc* desc, void* stream, hhg_shell** out);
 
+/* Several shells in one hierarchy: count descriptors that share
+ * tang_refine, radial_layers and fine_log2_intervals but may differ in their
+ * radii.  The shells become the disjoint components of one macro mesh, so
+ * every kernel of every call spans all of them (one launch where a single
+ * shell has one), and a V-cycle solves all of them together (its stopping
+ * test is on the residual of the whole group).  The budget of desc[0]
+ * applies to the group.  hhg_shell_part gives where shell k's nodes sit in
+ * the canonical vectors. */
+hhg_status hhg_setup_shells(const hhg_shell_desc* desc, int count, void* stream, hhg_shell** out);
+
+/* Shell k of a group on level L: start[t] and count[t] (nullable, 4 entries)
+ * of its nodes among the macro vertices (t = 0), edge nodes (1), face nodes
+ * (2) and cell-interior nodes (3) of the canonical vector; each range is
+ * contiguous and in the order of a single shell's canonical vector. */
+hhg_status hhg_shell_part(const hhg_shell* shell, int L, int k, int64_t* start, int64_t* count);
+
 /* Frees everything the shell owns (NULL is accepted). */
 hhg_status hhg_destroy(hhg_shell* shell);
 

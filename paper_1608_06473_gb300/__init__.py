@@ -75,6 +75,8 @@ _I = ctypes.c_int
 _SIGS = {
     "hhg_setup_shell": [ctypes.POINTER(hhg_shell_desc), _P, ctypes.POINTER(_P)],
     "hhg_destroy": [_P],
+    "hhg_setup_shells": [ctypes.POINTER(hhg_shell_desc), _I, _P, ctypes.POINTER(_P)],
+    "hhg_shell_part": [_P, _I, _I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "hhg_num_nodes": [_P, _I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "hhg_node_coords": [_P, _I, _P],
     "hhg_fit_surrogate": [_P, _I, _I, _P],
@@ -208,6 +210,23 @@ def hhg_setup_shell(r_inner=0.55, r_outer=1.0, tang_refine=0, radial_layers=1, f
     return h.value
 
 
+def hhg_setup_shells(radii, tang_refine=0, radial_layers=1, fine_log2_intervals=4, hbm_budget_bytes=0,
+                     stream=None) -> int:
+    """One hierarchy over several shells (radii: list of (r_inner, r_outer))."""
+    arr = (hhg_shell_desc * len(radii))(*[hhg_shell_desc(a, b, tang_refine, radial_layers, fine_log2_intervals,
+                                                         hbm_budget_bytes) for a, b in radii])
+    h = ctypes.c_void_p()
+    _check(lib().hhg_setup_shells(arr, len(radii), _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def hhg_shell_part(shell: int, L: int, k: int):
+    """[(start, count)] of shell k's vertex, edge, face and cell nodes on level L."""
+    st, ct = (ctypes.c_int64 * 4)(), (ctypes.c_int64 * 4)()
+    _check(lib().hhg_shell_part(shell, L, k, st, ct))
+    return [(st[t], ct[t]) for t in range(4)]
+
+
 def hhg_destroy(shell: int):
     _check(lib().hhg_destroy(shell))
 
@@ -278,6 +297,23 @@ class Shell:
         self.handle = hhg_setup_shell(r_inner, r_outer, tang_refine, radial_layers, fine_log2_intervals,
                                       hbm_budget_bytes, stream)
         self.L = fine_log2_intervals
+
+    @classmethod
+    def group(cls, radii, tang_refine=0, radial_layers=1, fine_log2_intervals=4, hbm_budget_bytes=0, stream=None):
+        """Several shells of the same macro topology and level, differing in
+        radii, as one hierarchy (every kernel launch spans all of them)."""
+        obj = cls.__new__(cls)
+        obj.handle = hhg_setup_shells(radii, tang_refine, radial_layers, fine_log2_intervals, hbm_budget_bytes,
+                                      stream)
+        obj.L = fine_log2_intervals
+        obj.n_parts = len(radii)
+        return obj
+
+    def part_index(self, k, L=None):
+        """Indices of shell k's nodes in the group's canonical vector, in the
+        order of that shell's own canonical vector."""
+        rng = hhg_shell_part(self.handle, self.L if L is None else L, k)
+        return np.concatenate([np.arange(s, s + c) for s, c in rng])
 
     def close(self):
         if self.handle:

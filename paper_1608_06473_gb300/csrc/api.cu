@@ -975,10 +975,48 @@ hhg_status hhg_timing_read(hhg_shell* s, int which, double* total_ms, int64_t* l
   });
 }
 
+static hhg_status setup_shells(const hhg_shell_desc* d, int count, void* stream, hhg_shell** out);
+
 hhg_status hhg_setup_shell(const hhg_shell_desc* d, void* stream, hhg_shell** out) {
+  return setup_shells(d, 1, stream, out);
+}
+
+hhg_status hhg_setup_shells(const hhg_shell_desc* d, int count, void* stream, hhg_shell** out) {
+  return setup_shells(d, count, stream, out);
+}
+
+hhg_status hhg_shell_part(const hhg_shell* s, int L, int k, int64_t* start, int64_t* count) {
   return guarded([&] {
-    HHG_CHECK(d && out, HHG_EINVAL, "NULL argument");
-    HHG_CHECK(d->r_inner > 0 && d->r_outer > d->r_inner, HHG_EINVAL, "need 0 < r_inner < r_outer");
+    const int n = level_index(const_cast<hhg_shell*>(s), L);
+    HHG_CHECK(k >= 0 && k < s->n_parts, HHG_EINVAL, "shell index out of range");
+    const LevelLayout& lay = s->levels[n].lay;
+    const int64_t per_e = lay.N - 1, per_f = lay.n_face, per_c = lay.n_int;
+    // every shell of the group has the same numbers of macro vertices, edges,
+    // faces and cells; its primitives follow those of the shells before it
+    const int64_t nV = lay.nV / s->n_parts, nE = lay.nE / s->n_parts, nF = lay.nF / s->n_parts,
+                  nC = lay.nC / s->n_parts;
+    const int64_t st4[4] = {k * nV, lay.off_E + k * nE * per_e, lay.off_F + k * nF * per_f, lay.off_C + k * nC * per_c};
+    const int64_t ct4[4] = {nV, nE * per_e, nF * per_f, nC * per_c};
+    for (int t = 0; t < 4; ++t) {
+      if (start) start[t] = st4[t];
+      if (count) count[t] = ct4[t];
+    }
+  });
+}
+
+static hhg_status setup_shells(const hhg_shell_desc* dd, int count, void* stream, hhg_shell** out) {
+  return guarded([&] {
+    HHG_CHECK(dd && out && count >= 1, HHG_EINVAL, "NULL argument or empty group");
+    const hhg_shell_desc* d = dd;
+    std::vector<std::pair<double, double>> radii;
+    for (int k = 0; k < count; ++k) {
+      const hhg_shell_desc& e = dd[k];
+      HHG_CHECK(e.r_inner > 0 && e.r_outer > e.r_inner, HHG_EINVAL, "need 0 < r_inner < r_outer");
+      HHG_CHECK(e.tang_refine == d->tang_refine && e.radial_layers == d->radial_layers &&
+                    e.fine_log2_intervals == d->fine_log2_intervals,
+                HHG_EINVAL, "the shells of a group must share tang_refine, radial_layers and the level");
+      radii.push_back({e.r_inner, e.r_outer});
+    }
     HHG_CHECK(d->tang_refine >= 0 && d->tang_refine <= 6, HHG_EINVAL, "tang_refine out of range");
     HHG_CHECK(d->radial_layers >= 1 && d->radial_layers <= 4096, HHG_EINVAL, "radial_layers out of range");
     HHG_CHECK(d->fine_log2_intervals >= 2 && d->fine_log2_intervals <= 10, HHG_EINVAL, "level out of range");
@@ -992,7 +1030,8 @@ hhg_status hhg_setup_shell(const hhg_shell_desc* d, void* stream, hhg_shell** ou
     hhg_shell* s = new hhg_shell();
     try {
       s->alloc.budget = d->hbm_budget_bytes;
-      s->mesh = build_shell(d->r_inner, d->r_outer, d->tang_refine, d->radial_layers);
+      s->mesh = build_shells(radii, d->tang_refine, d->radial_layers);
+      s->n_parts = count;
       s->Lf = d->fine_log2_intervals;
       std::vector<CellGeom> geom(s->mesh.nC());
       for (int c = 0; c < s->mesh.nC(); ++c)

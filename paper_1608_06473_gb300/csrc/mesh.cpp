@@ -86,9 +86,16 @@ void refine_sphere(std::vector<V3>& xs, std::vector<std::array<int, 3>>& tris) {
 }  // namespace
 
 MacroMesh build_shell(double r1, double r2, int tang, int layers) {
+  return build_shells({{r1, r2}}, tang, layers);
+}
+
+// Several shells as one macro mesh of disjoint components: shell s gets the
+// vertex ids after those of shells 0..s-1, so its vertices, edges, faces and
+// cells follow theirs in every primitive class.
+MacroMesh build_shells(const std::vector<std::pair<double, double>>& radii_in, int tang, int layers) {
   MacroMesh m;
-  m.r1 = r1;
-  m.r2 = r2;
+  m.r1 = radii_in.front().first;
+  m.r2 = radii_in.front().second;
   m.tang = tang;
   m.layers = layers;
   std::vector<V3> xs;
@@ -97,24 +104,28 @@ MacroMesh build_shell(double r1, double r2, int tang, int layers) {
   for (int t = 0; t < tang; ++t) refine_sphere(xs, tris);
   const int nS = (int)xs.size();
   m.nS = nS;
-  std::vector<double> radii(layers + 1);
-  for (int l = 0; l <= layers; ++l) radii[l] = r1 + (r2 - r1) * l / layers;
-  for (int l = 0; l <= layers; ++l)
-    for (int s = 0; s < nS; ++s) {
-      m.vx.push_back({radii[l] * xs[s][0], radii[l] * xs[s][1], radii[l] * xs[s][2]});
-      m.vr.push_back(radii[l]);
-      m.vlayer.push_back(l);
-    }
-  for (int l = 0; l < layers; ++l)
-    for (auto& t : tris) {
-      const int b0 = l * nS + t[0], b1 = l * nS + t[1], b2 = l * nS + t[2];
-      const int t0 = b0 + nS, t1 = b1 + nS, t2 = b2 + nS;
-      std::array<int, 4> cs[3] = {{b0, b1, b2, t2}, {b0, b1, t1, t2}, {b0, t0, t1, t2}};
-      for (auto& c : cs) {
-        std::sort(c.begin(), c.end());
-        m.cells.push_back(c);
+  for (const auto& rr : radii_in) {
+    const double r1 = rr.first, r2 = rr.second;
+    const int vo = (int)m.vx.size();
+    std::vector<double> radii(layers + 1);
+    for (int l = 0; l <= layers; ++l) radii[l] = r1 + (r2 - r1) * l / layers;
+    for (int l = 0; l <= layers; ++l)
+      for (int s = 0; s < nS; ++s) {
+        m.vx.push_back({radii[l] * xs[s][0], radii[l] * xs[s][1], radii[l] * xs[s][2]});
+        m.vr.push_back(radii[l]);
+        m.vlayer.push_back(l);
       }
-    }
+    for (int l = 0; l < layers; ++l)
+      for (auto& t : tris) {
+        const int b0 = vo + l * nS + t[0], b1 = vo + l * nS + t[1], b2 = vo + l * nS + t[2];
+        const int t0 = b0 + nS, t1 = b1 + nS, t2 = b2 + nS;
+        std::array<int, 4> cs[3] = {{b0, b1, b2, t2}, {b0, b1, t1, t2}, {b0, t0, t1, t2}};
+        for (auto& c : cs) {
+          std::sort(c.begin(), c.end());
+          m.cells.push_back(c);
+        }
+      }
+  }
   std::set<std::array<int, 2>> es;
   std::set<std::array<int, 3>> fs;
   for (auto& c : m.cells) {

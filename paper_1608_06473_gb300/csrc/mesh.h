@@ -8,6 +8,7 @@
 #include <array>
 #include <cstdint>
 #include <map>
+#include <utility>
 #include <vector>
 
 namespace hhg {
@@ -45,6 +46,7 @@ struct MacroMesh {
 };
 
 MacroMesh build_shell(double r1, double r2, int tang, int layers);
+MacroMesh build_shells(const std::vector<std::pair<double, double>>& radii, int tang, int layers);
 
 // Canonical layout of the nodes of one level (N intervals per macro edge).
 struct LevelLayout {

@@ -168,6 +168,7 @@ HD int line_id(int j, int k, int N) { return (k - 1) * (N - 2) - k * (k - 1) / 2
 struct hhg_shell {
   hhg::MacroMesh mesh;
   int Lf = 0;                          // finest log2(N)
+  int n_parts = 1;                     // shells of the group (disjoint components of the macro mesh)
   std::vector<hhg::Level> levels;      // levels[n]: N = 4 << n
   hhg::CellGeom* d_geom = nullptr;
   hhg::Allocator alloc;
