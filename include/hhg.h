@@ -107,6 +107,9 @@ typedef struct {
   int radial_layers;             /* >= 1 */
   int fine_log2_intervals;       /* finest L (N = 2^L), 2..10 */
   size_t hbm_budget_bytes;       /* 0 = no limit beyond the device */
+  int unprojected;               /* 0: nodes blended onto the shell (Phi, Sec. 2.2);
+                                    1: the unprojected polyhedral domain Omega_H
+                                    (Phi = Id), the paper's CONS operator (Sec. 4.1) */
 } hhg_shell_desc;
 
 /* Builds the macro mesh, its primitive graph and, for every level L = 2 ..

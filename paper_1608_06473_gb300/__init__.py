@@ -49,7 +49,7 @@ class HHGError(RuntimeError):
 class hhg_shell_desc(ctypes.Structure):
     _fields_ = [("r_inner", ctypes.c_double), ("r_outer", ctypes.c_double), ("tang_refine", ctypes.c_int),
                 ("radial_layers", ctypes.c_int), ("fine_log2_intervals", ctypes.c_int),
-                ("hbm_budget_bytes", ctypes.c_size_t)]
+                ("hbm_budget_bytes", ctypes.c_size_t), ("unprojected", ctypes.c_int)]
 
 
 class hhg_server_desc(ctypes.Structure):
@@ -203,8 +203,9 @@ def _stream(stream) -> int:
 
 
 def hhg_setup_shell(r_inner=0.55, r_outer=1.0, tang_refine=0, radial_layers=1, fine_log2_intervals=4,
-                    hbm_budget_bytes=0, stream=None) -> int:
-    d = hhg_shell_desc(r_inner, r_outer, tang_refine, radial_layers, fine_log2_intervals, hbm_budget_bytes)
+                    hbm_budget_bytes=0, stream=None, unprojected=False) -> int:
+    d = hhg_shell_desc(r_inner, r_outer, tang_refine, radial_layers, fine_log2_intervals, hbm_budget_bytes,
+                       int(bool(unprojected)))
     h = ctypes.c_void_p()
     _check(lib().hhg_setup_shell(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
     return h.value
@@ -293,9 +294,9 @@ class Shell:
     """Owning handle around hhg_setup_shell / hhg_destroy."""
 
     def __init__(self, r_inner=0.55, r_outer=1.0, tang_refine=0, radial_layers=1, fine_log2_intervals=4,
-                 hbm_budget_bytes=0, stream=None):
+                 hbm_budget_bytes=0, stream=None, unprojected=False):
         self.handle = hhg_setup_shell(r_inner, r_outer, tang_refine, radial_layers, fine_log2_intervals,
-                                      hbm_budget_bytes, stream)
+                                      hbm_budget_bytes, stream, unprojected)
         self.L = fine_log2_intervals
 
     @classmethod

@@ -1013,7 +1013,7 @@ static hhg_status setup_shells(const hhg_shell_desc* dd, int count, void* stream
       const hhg_shell_desc& e = dd[k];
       HHG_CHECK(e.r_inner > 0 && e.r_outer > e.r_inner, HHG_EINVAL, "need 0 < r_inner < r_outer");
       HHG_CHECK(e.tang_refine == d->tang_refine && e.radial_layers == d->radial_layers &&
-                    e.fine_log2_intervals == d->fine_log2_intervals,
+                    e.fine_log2_intervals == d->fine_log2_intervals && e.unprojected == d->unprojected,
                 HHG_EINVAL, "the shells of a group must share tang_refine, radial_layers and the level");
       radii.push_back({e.r_inner, e.r_outer});
     }
@@ -1031,6 +1031,7 @@ static hhg_status setup_shells(const hhg_shell_desc* dd, int count, void* stream
     try {
       s->alloc.budget = d->hbm_budget_bytes;
       s->mesh = build_shells(radii, d->tang_refine, d->radial_layers);
+      s->mesh.blend = d->unprojected == 0;
       s->n_parts = count;
       s->Lf = d->fine_log2_intervals;
       std::vector<CellGeom> geom(s->mesh.nC());
@@ -1038,7 +1039,7 @@ static hhg_status setup_shells(const hhg_shell_desc* dd, int count, void* stream
         for (int a = 0; a < 4; ++a) {
           const int v = s->mesh.cells[c][a];
           for (int x = 0; x < 3; ++x) geom[c].x[a][x] = s->mesh.vx[v][x];
-          geom[c].r[a] = s->mesh.vr[v];
+          geom[c].r[a] = s->mesh.blend ? s->mesh.vr[v] : -1.0;  // negative: no blending
         }
       s->d_geom = upload(s->alloc, geom, st);
       HHG_CUDA(cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking));

@@ -17,9 +17,9 @@
 //    per colour.
 //  * FP32: per plane k each direction's polynomial is reduced to a
 //    polynomial in (i, j) at fit time (FP32 table) and evaluated per node
-//    from shared memory.  The smoother stages the cell's planes in shared
-//    memory and runs the four colours in one launch (stage.cu); apply and
-//    residual are thread-per-node kernels here.
+//    from shared memory, thread per node, one launch per colour.  The
+//    smoother may instead run as the shared-memory staged one-launch sweep
+//    of stage.cu; a tuner times both per level and picks (lv.smooth_cfg).
 //
 // IFEM (Sec. 4.2.1): every node assembles its 15 weights from the 24 element
 // matrices around it (thread per node, one launch per colour).
@@ -40,6 +40,10 @@ namespace hhg {
 namespace {
 
 constexpr int NODE_THREADS = 256;  // thread-per-node kernels
+// FP64 surrogate kernel: 512 threads x 2 CTAs per SM (64 registers a thread,
+// 32 warps) measured 10% faster than 256 x 3 (80 registers) on GB300: the
+// kernel waits on memory, more warps hide it.
+constexpr int NODE64_THREADS = 512;
 
 // Coefficients of the polynomial in i along line (j, k): c_a(j, k) =
 // sum_{b,d} A_{a,b,d} j^b k^d.  Storage order of A (per direction):
@@ -392,7 +396,7 @@ __global__ void __launch_bounds__(NODE_THREADS, 2) lsqp_node_batch_kernel(LevelV
 }
 
 template <int Q, Mode MODE>
-__global__ void __launch_bounds__(NODE_THREADS, 3) lsqp_node_kernel(LevelView<double> lv, const uint32_t* __restrict__ list,
+__global__ void __launch_bounds__(NODE64_THREADS, 2) lsqp_node_kernel(LevelView<double> lv, const uint32_t* __restrict__ list,
                                                                   int n_list, double* u, double* out, const double* f,
                                                                   double* partial) {
   const int c = blockIdx.x;
@@ -677,7 +681,7 @@ void launch_node64(const LevelView<double>& lv, const uint32_t* list, int n, dou
                    double* partial, cudaStream_t st) {
   HHG_CHECK(lv.line64 != nullptr, HHG_ENOTFIT, "FP64 surrogate line table missing");
   if (lv.nrhs == 1) {
-    lsqp_node_kernel<Q, MODE><<<lv.nC, NODE_THREADS, 0, st>>>(lv, list, n, u, out, f, partial);
+    lsqp_node_kernel<Q, MODE><<<lv.nC, NODE64_THREADS, 0, st>>>(lv, list, n, u, out, f, partial);
     HHG_CUDA(cudaGetLastError());
     count_launch();
     return;

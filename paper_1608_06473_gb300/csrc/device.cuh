@@ -53,7 +53,9 @@ HD constexpr int DJ(int w) {
 }
 HD constexpr int DK(int w) { return (w >= 6 && w <= 9) ? 1 : ((w >= 10 && w <= 13) ? -1 : 0); }
 
-// Phi applied to the cell-local point (i, j, k) (Sec. 2.2): the affine point
+// Phi applied to the cell-local point (i, j, k) (Sec. 2.2), or the identity
+// for an unprojected shell (the CONS operator on the polyhedral domain, Sec.
+// 4.1; flagged by negative radii in the cell's geometry): the affine point
 // sum_a lam_a v_a / N moved along its ray to radius sum_a lam_a r_a / N.
 // Terms are accumulated in ascending vertex id, so a point shared by several
 // cells gets the same position from each of them.
@@ -67,8 +69,10 @@ __device__ __forceinline__ void mapped_point(const CellGeom& g, int i, int j, in
     x2 = fma(lam[a], g.x[a][2], x2);
     rho = fma(lam[a], g.r[a], rho);
   }
-  // X = (rho / N) x / |x| with x, rho the unscaled sums (1/N is exact)
-  const double s = (rho / (double)N) / sqrt(fma(x0, x0, fma(x1, x1, x2 * x2)));
+  // X = (rho / N) x / |x| with x, rho the unscaled sums (1/N is exact); a
+  // cell of an unprojected shell (radii stored negative) keeps the affine
+  // point x / N
+  const double s = g.r[0] < 0.0 ? 1.0 / (double)N : (rho / (double)N) / sqrt(fma(x0, x0, fma(x1, x1, x2 * x2)));
   X[0] = s * x0;
   X[1] = s * x1;
   X[2] = s * x2;

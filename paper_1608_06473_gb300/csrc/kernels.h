@@ -21,8 +21,9 @@ void ensure_smem_limit(const void* func, size_t bytes);
 //   APPLY:    out = L u on the interior nodes
 //   RESIDUAL: out = f - L u, partial[c] = sum of out^2 over cell c (nC slots)
 //   SMOOTH:   the four colour steps (i + 2j + 3k) mod 4 = 0..3 of Eq. 5.1,
-//             u updated in place (FP64: one launch per colour; FP32: one
-//             plane-wavefront launch).
+//             u updated in place (one launch per colour, or for FP32 the
+//             staged one-launch sweep where the tuner chose it, lv.smooth_cfg).
+// lv.nrhs right-hand sides per call (RESIDUAL partials at b pstride + c).
 // op: 0 = IFEM (on-the-fly exact stencils), 1 = LSQP (surrogate).
 template <class T>
 void launch_cell(const LevelView<T>& lv, int op, Mode mode, T* u, T* out, const T* f, double* partial,

@@ -239,6 +239,10 @@ void blend_point(const MacroMesh& m, int d, const int* g, const int* lam, int N,
     rho = rho + l * m.vr[g[a]];
   }
   for (int c = 0; c < 3; ++c) xh[c] = xh[c] / N;
+  if (!m.blend) {  // unprojected shell: Phi = Id
+    for (int c = 0; c < 3; ++c) out[c] = xh[c];
+    return;
+  }
   rho = rho / N;
   const double nrm = std::sqrt(xh[0] * xh[0] + xh[1] * xh[1] + xh[2] * xh[2]);
   for (int c = 0; c < 3; ++c) out[c] = rho * xh[c] / nrm;

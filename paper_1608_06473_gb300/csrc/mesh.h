@@ -15,6 +15,7 @@ namespace hhg {
 
 struct MacroMesh {
   double r1 = 0, r2 = 0;
+  bool blend = true;                             // false: nodes stay on the polyhedral macro mesh (Phi = Id)
   int tang = 0, layers = 1;
   int nS = 0;                                    // surface vertices
   std::vector<std::array<double, 3>> vx;         // macro vertex positions
