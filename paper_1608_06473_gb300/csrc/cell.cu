@@ -44,6 +44,9 @@ constexpr int NODE_THREADS = 256;  // thread-per-node kernels
 // 32 warps) measured 10% faster than 256 x 3 (80 registers) on GB300: the
 // kernel waits on memory, more warps hide it.
 constexpr int NODE64_THREADS = 512;
+// FP32 surrogate kernel: 512 threads x 2 CTAs per SM measured 4% (N = 64) and
+// 14% (N = 128) faster than 256 x 4 on GB300.
+constexpr int NODE32_THREADS = 512;
 
 // Coefficients of the polynomial in i along line (j, k): c_a(j, k) =
 // sum_{b,d} A_{a,b,d} j^b k^d.  Storage order of A (per direction):
@@ -453,7 +456,7 @@ __global__ void lsqp_plane_table_kernel(const double* __restrict__ coef, int nC,
 }
 
 template <int Q, Mode MODE>
-__global__ void __launch_bounds__(NODE_THREADS, 4) lsqp_node32_kernel(LevelView<float> lv,
+__global__ void __launch_bounds__(NODE32_THREADS, 2) lsqp_node32_kernel(LevelView<float> lv,
                                                                      const uint32_t* __restrict__ list, int n_list,
                                                                      float* u, float* out, const float* f,
                                                                      double* partial) {
@@ -716,7 +719,7 @@ void launch_node32(const LevelView<float>& lv, const uint32_t* list, int n, floa
   if (lv.nrhs == 1) {
     auto kern = lv.smooth_cfg == -2 ? lsqp_node32_x2_kernel<Q, MODE> : lsqp_node32_kernel<Q, MODE>;
     ensure_smem_limit((const void*)kern, smem);
-    kern<<<lv.nC, NODE_THREADS, smem, st>>>(lv, list, n, u, out, f, partial);
+    kern<<<lv.nC, lv.smooth_cfg == -2 ? NODE_THREADS : NODE32_THREADS, smem, st>>>(lv, list, n, u, out, f, partial);
     HHG_CUDA(cudaGetLastError());
     count_launch();
     return;
