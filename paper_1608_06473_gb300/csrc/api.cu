@@ -1378,7 +1378,9 @@ static int solve_batch(hhg_shell* s, int op, int dtype, const double* f, double*
   auto cycle = [&](cudaStream_t cs) {
     if (dd) HHG_CUDA(cudaMemcpyAsync(uprev, u, sizeof(double) * nt * nb, cudaMemcpyDeviceToDevice, cs));
     if (dtype == HHG_F32) {
-      // iterative refinement: e = one FP32 V-cycle on L e = r (e0 = 0), u += e
+      // iterative refinement: e = one FP32 V-cycle on L e = r (e0 = 0), u += e;
+      // double discretisation checks updates, not residuals, so r is formed here
+      if (dd) op_residual(s, n, op, u, f, Lv.d_r, 11, cs);
       launch_copy_cast<float>(Lv.d_r, Lv.d_f32, nt * nb, cs);
       HHG_CUDA(cudaMemsetAsync(Lv.d_u32, 0, sizeof(float) * nt * nb, cs));
       vcycle_rec32(s, n, op, Lv.d_f32, Lv.d_u32, nu1, nu2, cs);

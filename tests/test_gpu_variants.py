@@ -83,3 +83,20 @@ def test_dd_stops_on_updates_like_the_oracle(shell):
     assert relres[0] <= 1e-8
     assert abs(cycles - len(hist)) <= 1
     assert rel(ut.cpu().numpy(), u_ref, lv.free) <= 1e-7
+
+
+def test_dd_mixed_precision_matches_fp64_dd(shell):
+    """Double discretisation inside mixed-precision refinement (FP32 cycles on
+    the exact residual formed in FP64 each cycle): reaches the update
+    tolerance and the FP64 double-discretisation iterate to 1e-6."""
+    sh, s = shell
+    s.fit(2, 2)
+    n, _ = s.num_nodes()
+    f = torch.from_numpy(synthetic.uniform(n, synthetic.SEED_F)).cuda()
+    u64, u32 = torch.zeros_like(f), torch.zeros_like(f)
+    rel64, _, _ = s.vcycle(f, u64, rtol=1e-8, op=hhg.HHG_OP_DD, dtype=hhg.HHG_F64, max_cycles=40)
+    rel32, _, _ = s.vcycle(f, u32, rtol=1e-8, op=hhg.HHG_OP_DD, dtype=hhg.HHG_F32, max_cycles=40)
+    torch.cuda.synchronize()
+    assert rel64[0] <= 1e-8 and rel32[0] <= 1e-8
+    free = M.make_level(sh, 2 ** L).free
+    assert rel(u32.cpu().numpy(), u64.cpu().numpy(), free) <= 1e-6
