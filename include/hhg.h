@@ -162,6 +162,25 @@ hhg_status hhg_fit_surrogate(hhg_shell* shell, int q, int j, void* stream);
  * HHG_OP_DD then use these polynomials. */
 hhg_status hhg_fit_ipoly(hhg_shell* shell, void* stream);
 
+/* CONS stencils as the cell-interior surrogate (Sec. 4.1, "CONS DD"): the
+ * polynomials of hhg_fit_surrogate fitted to the stencils of the unprojected
+ * domain Omega_H (Phi = Id), which are constant per macro cell and so
+ * reproduced by every q.  Replaces any previous fit.  With HHG_OP_DD the
+ * relaxation then uses these stencils in the cell interiors (vertex, edge
+ * and face rows stay exact) and the residuals the exact operator. */
+hhg_status hhg_fit_cons(hhg_shell* shell, int q, int j, void* stream);
+
+/* Load vector of the accuracy study (Sec. 4): b_I = V_I f_I for every
+ * unknown I of level L, with V_I the sum of |T| / 4 over the fine tetrahedra
+ * T containing node I (vertex quadrature on each tetrahedron of the blended
+ * mesh; of the straight mesh for an unprojected shell), and b_I = 0 at
+ * Dirichlet nodes.  f holds the values of the right-hand-side function at
+ * the nodes (canonical order, n_total doubles; host or device); b the same
+ * size; f and b must not overlap.  The first call per level builds the
+ * incidence of the lower nodes in the cells on the host (kept until
+ * hhg_destroy). */
+hhg_status hhg_load_vector(hhg_shell* shell, int L, const double* f, double* b, void* stream);
+
 /* y = L_L u (op = IFEM) or y = L~_L u (op = LSQP) on level L, for nrhs
  * vectors (Sec. 3.4, the operator of Eq. 3.4).  u and y must not overlap. */
 hhg_status hhg_apply(hhg_shell* shell, int L, hhg_op op, hhg_dtype dtype,

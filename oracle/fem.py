@@ -116,3 +116,35 @@ def free_block(A: sp.csr_matrix, level: M.Level) -> sp.csr_matrix:
     """A with the Dirichlet rows and columns removed (the unknowns only)."""
     f = level.free
     return A[f][:, f].tocsr()
+
+
+def lumped_mass(level: M.Level) -> np.ndarray:
+    """Vertex-quadrature weight of every canonical node: V_I = sum over the
+    fine tetrahedra T containing node I of |T| / 4 (the row sums of the P1
+    mass matrix).  Tetrahedra are straight with the level's node positions
+    (mapped or not)."""
+    loc = cell_tet_nodes(level.N)
+    V = np.zeros(level.n_total)
+    for chunk in np.array_split(np.arange(level.shell.nC), max(1, level.shell.nC // 64)):
+        glob = level.cell_map[chunk][:, loc].reshape(-1, 4)
+        P = level.coords[glob]
+        vol = np.abs(np.linalg.det(P[:, 1:, :] - P[:, :1, :])) / 6.0
+        for a in range(4):
+            V += np.bincount(glob[:, a], weights=vol / 4.0, minlength=level.n_total)
+    return V
+
+
+def load_vector(level: M.Level, f_nodes: np.ndarray) -> np.ndarray:
+    """Right-hand side of the accuracy study (Sec. 4): b_I = integral of f
+    phi_I by the vertex quadrature rule on every tetrahedron, b_I = V_I f(x_I),
+    for the unknowns; 0 at Dirichlet nodes."""
+    b = np.zeros(level.n_total)
+    fr = level.free
+    b[fr] = lumped_mass(level)[fr] * f_nodes[fr]
+    return b
+
+
+def discretisation_error(level: M.Level, u_exact: np.ndarray, v: np.ndarray) -> float:
+    """e = h^(3/2) ||I_l(u) - v||_2 of Sec. 4.2 over all nodes, with
+    h = 1/N (the macro mesh size H taken as 1)."""
+    return (1.0 / level.N) ** 1.5 * float(np.linalg.norm(u_exact - v))

@@ -124,9 +124,14 @@ def evaluate(coef: np.ndarray, pts: np.ndarray, N: int, q: int) -> np.ndarray:
 def surrogate_operator(level: M.Level, A: sp.csr_matrix, coef: np.ndarray, q: int) -> sp.csr_matrix:
     """L~_l: A with every cell-interior row replaced by the surrogate stencil
     (Sec. 3.4); rows of vertex, edge and face nodes are kept exact."""
+    return with_interior_stencils(level, A, evaluate(coef, M.interior_points(level.N), level.N, q))
+
+
+def with_interior_stencils(level: M.Level, A: sp.csr_matrix, S: np.ndarray) -> sp.csr_matrix:
+    """A with the row of every cell-interior node replaced by the 15 weights
+    S (n_cells, n_l, 15) in the named directions; lower rows kept."""
     N = level.N
     ip = M.interior_points(N)
-    S = evaluate(coef, ip, N, q)                    # (nC, n_l, 15)
     Ac = A.tocoo()
     keep = Ac.row < level.off_C
     rows, cols, vals = [Ac.row[keep]], [Ac.col[keep]], [Ac.data[keep]]

@@ -247,22 +247,29 @@ class Hierarchy:
         return u, hist
 
 
-def build_hierarchy(shell: M.Shell, N_fine: int, op: str = "lsqp", q: int = 2, j: int = 2):
+def build_hierarchy(shell: M.Shell, N_fine: int, op: str = "lsqp", q: int = 2, j: int = 2,
+                    mapped: bool = True):
     """Levels, operators and transfers for a shell: op = 'ifem' (exact),
-    'lsqp' or 'ipoly' (surrogate on N >= 8), or 'dd-lsqp' / 'dd-ipoly'
-    (double discretisation: surrogate sweeps, exact residuals)."""
+    'lsqp' or 'ipoly' (surrogate on N >= 8), 'dd-lsqp' / 'dd-ipoly' (double
+    discretisation: surrogate sweeps, exact residuals) or 'dd-cons' (CONS DD
+    of Sec. 4.1: sweeps whose cell-interior rows are the stencils of the
+    unprojected domain, exact residuals).  mapped = False builds every level
+    on the unprojected domain (with 'ifem': the CONS operator)."""
     from . import fem as F
     from . import lsqp as LS
     levels, ops, sms = [], [], []
     N = 4
     while N <= N_fine:
-        lv = M.make_level(shell, N)
+        lv = M.make_level(shell, N, mapped=mapped)
         A = F.assemble(lv)
         S = A
         kind = op.split("-")[-1]
         if kind in ("lsqp", "ipoly") and N >= 8:
             coef = LS.fit(lv, A, q, j) if kind == "lsqp" else LS.fit_ipoly(lv, A)
             S = LS.surrogate_operator(lv, A, coef, q if kind == "lsqp" else 2)
+        elif kind == "cons" and N >= 8:
+            lu = M.make_level(shell, N, mapped=False)
+            S = LS.with_interior_stencils(lv, A, F.interior_stencils(lu, F.assemble(lu)))
         levels.append(lv)
         ops.append(Operator(lv, A if op.startswith("dd-") else S))
         sms.append(Operator(lv, S))

@@ -81,6 +81,8 @@ _SIGS = {
     "hhg_node_coords": [_P, _I, _P],
     "hhg_fit_surrogate": [_P, _I, _I, _P],
     "hhg_fit_ipoly": [_P, _P],
+    "hhg_fit_cons": [_P, _I, _I, _P],
+    "hhg_load_vector": [_P, _I, _P, _P, _P],
     "hhg_apply": [_P, _I, _I, _I, _P, _P, _I, _P],
     "hhg_residual": [_P, _I, _I, _I, _P, _P, _P, _I, _P, _P],
     "hhg_smooth": [_P, _I, _I, _I, _P, _P, _I, _I, _P],
@@ -253,6 +255,14 @@ def hhg_fit_ipoly(shell: int, stream=None):
     _check(lib().hhg_fit_ipoly(shell, _stream(stream)))
 
 
+def hhg_fit_cons(shell: int, q: int = 2, j: int = 2, stream=None):
+    _check(lib().hhg_fit_cons(shell, q, j, _stream(stream)))
+
+
+def hhg_load_vector(shell: int, L: int, f, b, stream=None):
+    _check(lib().hhg_load_vector(shell, L, _ptr(f), _ptr(b), _stream(stream)))
+
+
 def hhg_apply(shell: int, L: int, op: int, dtype: int, u, y, nrhs: int = 1, stream=None):
     _check(lib().hhg_apply(shell, L, op, dtype, _ptr(u), _ptr(y), nrhs, _stream(stream)))
 
@@ -344,6 +354,12 @@ class Shell:
 
     def fit_ipoly(self, stream=None):
         hhg_fit_ipoly(self.handle, stream)
+
+    def fit_cons(self, q=2, j=2, stream=None):
+        hhg_fit_cons(self.handle, q, j, stream)
+
+    def load_vector(self, f, b, L=None, stream=None):
+        hhg_load_vector(self.handle, self.L if L is None else L, f, b, stream)
 
     def apply(self, u, y, L=None, op=HHG_OP_LSQP, dtype=HHG_F64, nrhs=1, stream=None):
         hhg_apply(self.handle, self.L if L is None else L, op, dtype, u, y, nrhs, stream)

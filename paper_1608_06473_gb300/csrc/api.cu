@@ -139,6 +139,47 @@ static void parents(int d, const int* lam, int* pa, int* pb) {
   for (int a = 0; a < d; ++a) { pa[a] /= 2; pb[a] /= 2; }
 }
 
+// Points of the closed macro cell that are not interior (its faces, edges
+// and vertices), in lin_full order, and each full position's slot among them
+// (-1 for interior points).
+static void boundary_points(int N, std::vector<uint32_t>& bnd_ijk, std::vector<int>& bnd_slot) {
+  bnd_ijk.clear();
+  bnd_slot.assign((size_t)tet_points(N), -1);
+  for (int k = 0; k <= N; ++k)
+    for (int j = 0; j <= N - k; ++j)
+      for (int i = 0; i <= N - j - k; ++i)
+        if (!is_interior(i, j, k, N)) {
+          bnd_slot[lin_full(i, j, k, N)] = (int)bnd_ijk.size();
+          bnd_ijk.push_back(pack_ijk(i, j, k));
+        }
+}
+
+// Halo sources (canonical index of every cell boundary point, -1 where it is
+// a Dirichlet node) and the incidence of the lower nodes in the cells: for
+// lower node r, inc_cb[inc_ptr[r] .. inc_ptr[r+1]) are the (cell * n_bnd +
+// slot) positions holding it, in ascending cell order.  Dirichlet nodes have
+// no incidence.
+static void lower_incidence(const MacroMesh& m, const LevelLayout& lay, const std::vector<uint32_t>& bnd_ijk,
+                            std::vector<int>& halo_src, std::vector<int64_t>& inc_ptr, std::vector<int>& inc_cb) {
+  const int n_bnd = (int)bnd_ijk.size();
+  const int64_t nhal = lay.nC * n_bnd;
+  halo_src.assign((size_t)nhal, -1);
+  inc_ptr.assign((size_t)lay.off_C + 1, 0);
+  for (int c = 0; c < lay.nC; ++c)
+    for (int b = 0; b < n_bnd; ++b) {
+      const uint32_t p = bnd_ijk[b];
+      const int64_t idx = cell_node_index(m, lay, c, unpack_i(p), unpack_j(p), unpack_k(p));
+      const bool dir = node_dirichlet(m, lay, idx);
+      halo_src[(size_t)c * n_bnd + b] = dir ? -1 : (int)idx;
+      if (!dir) inc_ptr[idx + 1]++;
+    }
+  for (int64_t r = 0; r < lay.off_C; ++r) inc_ptr[r + 1] += inc_ptr[r];
+  inc_cb.assign((size_t)inc_ptr[lay.off_C], 0);
+  std::vector<int64_t> fill(inc_ptr.begin(), inc_ptr.end() - 1);
+  for (int64_t t = 0; t < nhal; ++t)
+    if (halo_src[t] >= 0) inc_cb[fill[halo_src[t]]++] = (int)t;
+}
+
 static void build_level(hhg_shell* s, int n, cudaStream_t st) {
   const MacroMesh& m = s->mesh;
   Level& L = s->levels[n];
@@ -208,36 +249,16 @@ static void build_level(hhg_shell* s, int n, cudaStream_t st) {
         for (int i = 1; i < N - j - k; ++i)
           if (deep(i, j, k) == (pass == 0)) all_nodes.push_back(pack_ijk(i, j, k));
   std::vector<uint32_t> bnd_ijk;
-  std::vector<int> bnd_slot((size_t)lay.n_full, -1);
-  for (int k = 0; k <= N; ++k)
-    for (int j = 0; j <= N - k; ++j)
-      for (int i = 0; i <= N - j - k; ++i)
-        if (!is_interior(i, j, k, N)) {
-          bnd_slot[lin_full(i, j, k, N)] = (int)bnd_ijk.size();
-          bnd_ijk.push_back(pack_ijk(i, j, k));
-        }
+  std::vector<int> bnd_slot;
+  boundary_points(N, bnd_ijk, bnd_slot);
   L.n_bnd = (int)bnd_ijk.size();
   L.h_plane_off = plane_off;
 
   // halo sources and the incidence of lower nodes in cells
-  const int64_t nhal = lay.nC * L.n_bnd;
-  std::vector<int> halo_src((size_t)nhal);
-  std::vector<int64_t> inc_ptr((size_t)lay.off_C + 1, 0);
-  for (int c = 0; c < lay.nC; ++c)
-    for (int b = 0; b < L.n_bnd; ++b) {
-      const uint32_t p = bnd_ijk[b];
-      const int64_t idx = cell_node_index(m, lay, c, unpack_i(p), unpack_j(p), unpack_k(p));
-      const bool dir = node_dirichlet(m, lay, idx);
-      halo_src[(size_t)c * L.n_bnd + b] = dir ? -1 : (int)idx;
-      if (!dir) inc_ptr[idx + 1]++;
-    }
-  for (int64_t r = 0; r < lay.off_C; ++r) inc_ptr[r + 1] += inc_ptr[r];
-  std::vector<int> inc_cb((size_t)inc_ptr[lay.off_C]);
-  {
-    std::vector<int64_t> fill(inc_ptr.begin(), inc_ptr.end() - 1);
-    for (int64_t t = 0; t < nhal; ++t)
-      if (halo_src[t] >= 0) inc_cb[fill[halo_src[t]]++] = (int)t;
-  }
+  std::vector<int> halo_src;
+  std::vector<int64_t> inc_ptr;
+  std::vector<int> inc_cb;
+  lower_incidence(m, lay, bnd_ijk, halo_src, inc_ptr, inc_cb);
 
   // lower-primitive colour steps and Dirichlet list
   std::vector<int> steps[6], dirl;
@@ -779,10 +800,22 @@ static void vcycle_rec32(hhg_shell* s, int n, int op, const float* f, float* u, 
 // ipoly = false: LSQP on S_l = M_{m(l,j)} (Sec. 3.2); ipoly = true: IPOLY
 // (Sec. 3.1), q = 2 interpolation at the ten quadratic nodes of the macro
 // cell shrunk to its interior, a = N - 3, b = N/2 - 1 (the square system is
-// solved by the same QR).
-static void fit(hhg_shell* s, int q, int j, cudaStream_t st, bool ipoly = false) {
+// solved by the same QR).  unprojected = true samples the stencils of the
+// unprojected domain (Phi = Id; constant per cell, so every degree
+// reproduces them): the cell-interior rows of the CONS operator (Sec. 4.1).
+static void fit(hhg_shell* s, int q, int j, cudaStream_t st, bool ipoly = false, bool unprojected = false) {
   TimedScope all(s, -1, HHG_T_FIT, st);
   const int mq = n_coeffs(q);
+  const int64_t nC = s->levels.empty() ? 0 : s->levels[0].lay.nC;
+  CellGeom* d_geom_sample = s->d_geom;
+  if (unprojected) {  // the cells' geometry with the radii flagged negative (Phi = Id)
+    std::vector<CellGeom> g((size_t)nC);
+    HHG_CUDA(cudaMemcpyAsync(g.data(), s->d_geom, g.size() * sizeof(CellGeom), cudaMemcpyDeviceToHost, st));
+    HHG_CUDA(cudaStreamSynchronize(st));
+    for (CellGeom& c : g)
+      for (double& r : c.r) r = -std::fabs(r);
+    d_geom_sample = upload(s->alloc, g, st);
+  }
   for (size_t n = 0; n < s->levels.size(); ++n) {
     Level& L = s->levels[n];
     const int N = L.N;
@@ -842,7 +875,7 @@ static void fit(hhg_shell* s, int q, int j, cudaStream_t st, bool ipoly = false)
     for (int c0 = 0; c0 < L.lay.nC; c0 += chunk) {
       const int nc = (int)std::min<int64_t>(chunk, L.lay.nC - c0);
       LevelView<double> vc = v;
-      vc.geom = s->d_geom + c0;
+      vc.geom = d_geom_sample + c0;
       vc.nC = nc;
       launch_sample(vc, d_pts, np, d_b, st);
       launch_fit_coef(nc, mq, np, d_P, d_sc, d_b, L.d_coef + (int64_t)c0 * 15 * mq, L.d_coef32 + (int64_t)c0 * 15 * mq,
@@ -856,6 +889,7 @@ static void fit(hhg_shell* s, int q, int j, cudaStream_t st, bool ipoly = false)
     A.release(d_P);
     A.release(d_sc);
   }
+  if (unprojected) s->alloc.release(d_geom_sample);
   s->q = q;
   s->j = ipoly ? 0 : j;
   ++s->gen;
@@ -1156,6 +1190,15 @@ hhg_status hhg_fit_ipoly(hhg_shell* s, void* stream) {
   });
 }
 
+hhg_status hhg_fit_cons(hhg_shell* s, int q, int j, void* stream) {
+  return guarded([&] {
+    HHG_CHECK(s != nullptr, HHG_EINVAL, "NULL shell");
+    HHG_CHECK(q >= 1 && q <= 3, HHG_EINVAL, "q must be 1, 2 or 3");
+    HHG_CHECK(j >= 1, HHG_EINVAL, "j must be >= 1");
+    fit(s, q, j, (cudaStream_t)stream, false, true);
+  });
+}
+
 hhg_status hhg_fit_surrogate(hhg_shell* s, int q, int j, void* stream) {
   return guarded([&] {
     HHG_CHECK(s != nullptr, HHG_EINVAL, "NULL shell");
@@ -1262,6 +1305,29 @@ hhg_status hhg_apply(hhg_shell* s, int L, hhg_op op, hhg_dtype dtype, const void
       op_apply(s, n, op, au.dev, ay.dev, st);
       stage_out(ay, nt, st);
     }
+  });
+}
+
+hhg_status hhg_load_vector(hhg_shell* s, int L, const double* f, double* b, void* stream) {
+  return guarded([&] {
+    const int n = level_index(s, L);
+    HHG_CHECK(f != b, HHG_EINVAL, "f and b must not overlap");
+    cudaStream_t st = (cudaStream_t)stream;
+    Level& Lv = s->levels[n];
+    const int64_t nt = Lv.lay.n_total;
+    if (!Lv.d_inc_ptr) {  // the incidence is rebuilt on the host the first time
+      std::vector<uint32_t> bnd_ijk;
+      std::vector<int> bnd_slot, halo_src, inc_cb;
+      std::vector<int64_t> inc_ptr;
+      boundary_points(Lv.N, bnd_ijk, bnd_slot);
+      lower_incidence(s->mesh, Lv.lay, bnd_ijk, halo_src, inc_ptr, inc_cb);
+      Lv.d_inc_ptr = upload(s->alloc, inc_ptr, st);
+      Lv.d_inc_cb = upload(s->alloc, inc_cb, st);
+    }
+    Arg af = stage_in(s, 0, f, nt, true, st);
+    Arg ab = stage_in(s, 1, b, nt, false, st);
+    launch_load_vector(view<double>(s, n), Lv.d_inc_ptr, Lv.d_inc_cb, af.dev, ab.dev, st);
+    stage_out(ab, nt, st);
   });
 }
 

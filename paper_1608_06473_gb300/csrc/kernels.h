@@ -140,4 +140,8 @@ void launch_low_assemble(const LevelView<double>& lv, int pass, const int64_t* i
                          int* row_len, int64_t* sell_ptr, int* sell_col, double* sell_val, double* diag,
                          cudaStream_t st);
 
+// Load vector b = V f of the accuracy study (vertex quadrature; load.cu).
+void launch_load_vector(const LevelView<double>& lv, const int64_t* inc_ptr, const int* inc_cb, const double* f,
+                        double* b, cudaStream_t st);
+
 }  // namespace hhg

@@ -118,6 +118,9 @@ struct Level {
   int step_n[6] = {0, 0, 0, 0, 0, 0};
   int max_step = 0;
   int* d_dirichlet = nullptr;    // Dirichlet lower nodes
+  // incidence of the lower nodes in the cells (load vector; built on first use)
+  int64_t* d_inc_ptr = nullptr;
+  int* d_inc_cb = nullptr;
   int n_dirichlet = 0;
   int64_t n_free = 0;
   // transfers: coarse parents of this level's lower nodes (this level fine),
