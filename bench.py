@@ -66,7 +66,7 @@ def parse():
     p.add_argument("--j", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--mode", choices=["solve", "smoother", "serve", "variants"], default="solve",
+    p.add_argument("--mode", choices=["solve", "smoother", "serve", "variants", "discretisation"], default="solve",
                    help="solve: the whole path per step (default); smoother: finest-level sweeps only "
                         "(for profiling the smoother kernels)")
     p.add_argument("--op", choices=["lsqp", "ifem"], default="lsqp", help="operator for --mode smoother")
@@ -77,6 +77,8 @@ def parse():
                    help="f64: FP64 V-cycles; mixed: FP32 V-cycles inside FP64 iterative refinement")
     p.add_argument("--serve-requests", type=int, default=48,
                    help="requests of the serving stream reported beside the solve (0 = skip)")
+    p.add_argument("--disc-max-nodes", type=float, default=25e6,
+                   help="--mode discretisation: largest level (total nodes) of the study")
     p.add_argument("--compare-f64", action="store_true",
                    help="with --precision mixed: also time one plain FP64 solve and report the speedup")
     return p.parse_args()
@@ -513,6 +515,79 @@ def run_variants(args):
             "rtol": 1e-8, "variants": out}
 
 
+DISC_MESHES = {60: (0, 1), 480: (1, 2), 3840: (2, 4)}   # macro cells: (surface refinements, radial layers)
+DISC_VARIANTS = ("fem", "lsqp_q1", "lsqp_q2", "lsqp_q3", "ipoly", "lsqp_dd", "ipoly_dd", "cons", "cons_dd")
+
+
+def run_discretisation(args):
+    """The accuracy study of Sec. 4 (Table 4.1 and the DD / CONS comparison
+    of Sec. 4.2) on the GPU: for the 60-, 480- and 3840-cell shells
+    (r in [0.55, 1]) and levels L = 2.. (N = 2^(L+2)) up to --disc-max-nodes,
+    the exact solution u of Sec. 4 and f = -Laplace(u) at the nodes, the
+    vertex-quadrature load vector (hhg_load_vector), 10 V(3,3) cycles from
+    u = 0 per variant, and e = h^(3/2) ||I(u) - v||_2 over all nodes with
+    h = H/N and the macro mesh size H = 1, 1/2, 1/4 for the 60-, 480- and
+    3840-cell shells (each macro refinement halves it).  Variants: FEM (exact operator), LSQP q = 1, 2, 3, IPOLY, LSQP DD
+    and IPOLY DD (surrogate relaxation, exact residuals), CONS (the operator
+    of the unprojected domain, compared with u at its own nodes) and CONS DD
+    (relaxation with the unprojected stencils in the cell interiors).  dev =
+    e / e_FEM - 1; Table 4.1 sets entries with |dev| > 0.1 in italics."""
+    import torch
+
+    import paper_1608_06473_gb300 as hhg
+    import synthetic
+    r1, r2 = 0.55, 1.0
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    rows = []
+    for cells, (tang, layers) in DISC_MESHES.items():
+        for Lp in range(2, 7):
+            N = 2 ** (Lp + 2)
+            n_total, _ = hhg.hhg_problem_nodes(r1, r2, tang, layers, Lp + 2)
+            if n_total > args.disc_max_nodes:
+                break
+            row = {"cells": cells, "L": Lp, "N": N, "nodes": n_total, "e": {}, "dev": {}, "solve_s": {}}
+            for unproj in (False, True):
+                s = hhg.Shell(r1, r2, tang, layers, Lp + 2, stream=stream, unprojected=unproj)
+                X = torch.from_numpy(s.node_coords()).cuda()
+                ue, fe = synthetic.manufactured(X, r1, r2, xp=torch)
+                del X
+                b = torch.empty_like(fe)
+                s.load_vector(fe, b, stream=stream)
+                del fe
+                u = torch.empty_like(b)
+                plan = ([("cons", hhg.HHG_OP_LSQP, ("lsqp", 2))] if unproj else
+                        [("fem", hhg.HHG_OP_IFEM, None), ("lsqp_q1", hhg.HHG_OP_LSQP, ("lsqp", 1)),
+                         ("lsqp_q2", hhg.HHG_OP_LSQP, ("lsqp", 2)), ("lsqp_q3", hhg.HHG_OP_LSQP, ("lsqp", 3)),
+                         ("lsqp_dd", hhg.HHG_OP_DD, ("lsqp", 2)), ("ipoly", hhg.HHG_OP_LSQP, ("ipoly", 2)),
+                         ("ipoly_dd", hhg.HHG_OP_DD, ("ipoly", 2)), ("cons_dd", hhg.HHG_OP_DD, ("cons", 2))])
+                for name, op, fit in plan:
+                    if fit and fit[0] == "lsqp":
+                        s.fit(fit[1], 2, stream=stream)
+                    elif fit and fit[0] == "ipoly":
+                        s.fit_ipoly(stream=stream)
+                    elif fit:
+                        s.fit_cons(fit[1], 2, stream=stream)
+                    u.zero_()
+                    a, z = ev(), ev()
+                    a.record(stream)
+                    s.vcycle(b, u, max_cycles=10, rtol=0.0, op=op, stream=stream, raise_on_noconv=False)
+                    z.record(stream)
+                    torch.cuda.synchronize()
+                    row["solve_s"][name] = a.elapsed_time(z) * 1e-3
+                    row["e"][name] = (2.0 ** -tang / N) ** 1.5 * float(torch.linalg.vector_norm(ue - u))
+                s.close()
+                del ue, b, u
+                torch.cuda.empty_cache()
+            for name in DISC_VARIANTS:
+                row["dev"][name] = row["e"][name] / row["e"]["fem"] - 1
+            rows.append(row)
+            print(json.dumps({"cells": cells, "L": Lp, "e": row["e"]}), file=sys.stderr, flush=True)
+    return {"mode": "discretisation", "radii": [r1, r2], "cycles": "10 x V(3,3) from u = 0",
+            "h": "H/N, H = 1, 1/2, 1/4 for 60, 480, 3840 cells",
+            "load_vector": "vertex quadrature (hhg_load_vector)", "rows": rows}
+
+
 def run_smoother(args):
     """Finest-level smoother only: setup, fit, `warmup` sweeps, then `steps`
     sweeps timed with CUDA events on the launching stream."""
@@ -560,6 +635,9 @@ def main():
         return
     if args.mode == "variants":
         print(json.dumps(run_variants(args)))
+        return
+    if args.mode == "discretisation":
+        print(json.dumps(run_discretisation(args)))
         return
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))

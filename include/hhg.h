@@ -213,7 +213,11 @@ hhg_status hhg_smooth(hhg_shell* shell, int L, hhg_op op, hhg_dtype dtype,
  * smoothing with the surrogate, residuals with the exact stencils, and the
  * stopping test on the updates instead of the residual,
  * ||u_k - u_{k-1}||_2 <= rtol ||u_1 - u_0||_2, as that section recommends;
- * relres_out then holds that ratio. */
+ * relres_out then holds that ratio.  With HHG_F32 the FP64 refinement forms
+ * the exact residual every cycle and the FP32 cycle relaxes with the
+ * surrogate: that is defect correction, whose fixed point is the solution of
+ * the exact operator, not the fixed point of the FP64 double-discretisation
+ * cycle (the two differ by the inconsistency between the operators). */
 hhg_status hhg_vcycle(hhg_shell* shell, hhg_op op, hhg_dtype dtype,
                       const void* f, void* u, int nu1, int nu2, int max_cycles,
                       double rtol, int nrhs, double* relres_out, int* cycles_out,

@@ -85,18 +85,23 @@ def test_dd_stops_on_updates_like_the_oracle(shell):
     assert rel(ut.cpu().numpy(), u_ref, lv.free) <= 1e-7
 
 
-def test_dd_mixed_precision_matches_fp64_dd(shell):
-    """Double discretisation inside mixed-precision refinement (FP32 cycles on
-    the exact residual formed in FP64 each cycle): reaches the update
-    tolerance and the FP64 double-discretisation iterate to 1e-6."""
+def test_dd_mixed_precision_is_defect_correction(shell):
+    """Double discretisation inside mixed-precision refinement: the FP64
+    outer loop forms the exact residual f - L u every cycle and the FP32
+    cycle relaxes with the surrogate, so the refinement's fixed point is the
+    solution of the exact operator (defect correction), not the fixed point
+    of the FP64 double-discretisation cycle.  It reaches the update tolerance
+    and the exact (IFEM) FP64 solution to 1e-6; the oracle's defect
+    correction with its FP64 DD cycle shows the same fixed point (7e-13 from
+    the exact solution, 0.7 % from the DD iterate on this shell)."""
     sh, s = shell
     s.fit(2, 2)
     n, _ = s.num_nodes()
     f = torch.from_numpy(synthetic.uniform(n, synthetic.SEED_F)).cuda()
-    u64, u32 = torch.zeros_like(f), torch.zeros_like(f)
-    rel64, _, _ = s.vcycle(f, u64, rtol=1e-8, op=hhg.HHG_OP_DD, dtype=hhg.HHG_F64, max_cycles=40)
-    rel32, _, _ = s.vcycle(f, u32, rtol=1e-8, op=hhg.HHG_OP_DD, dtype=hhg.HHG_F32, max_cycles=40)
+    ue, u32 = torch.zeros_like(f), torch.zeros_like(f)
+    rele, _, _ = s.vcycle(f, ue, rtol=1e-11, op=hhg.HHG_OP_IFEM, dtype=hhg.HHG_F64, max_cycles=60)
+    rel32, _, _ = s.vcycle(f, u32, rtol=1e-9, op=hhg.HHG_OP_DD, dtype=hhg.HHG_F32, max_cycles=60)
     torch.cuda.synchronize()
-    assert rel64[0] <= 1e-8 and rel32[0] <= 1e-8
+    assert rele[0] <= 1e-11 and rel32[0] <= 1e-9
     free = M.make_level(sh, 2 ** L).free
-    assert rel(u32.cpu().numpy(), u64.cpu().numpy(), free) <= 1e-6
+    assert rel(u32.cpu().numpy(), ue.cpu().numpy(), free) <= 1e-6
