@@ -79,6 +79,10 @@ def parse():
                    help="requests of the serving stream reported beside the solve (0 = skip)")
     p.add_argument("--disc-max-nodes", type=float, default=25e6,
                    help="--mode discretisation: largest level (total nodes) of the study")
+    p.add_argument("--disc-cells", type=str, default="60,480,3840,30720",
+                   help="--mode discretisation: macro meshes (cell counts) of the study")
+    p.add_argument("--disc-min-level", type=int, default=2,
+                   help="--mode discretisation: first level L (N = 2^(L+2))")
     p.add_argument("--compare-f64", action="store_true",
                    help="with --precision mixed: also time one plain FP64 solve and report the speedup")
     return p.parse_args()
@@ -279,13 +283,12 @@ def run_ours(args, rank, world, local):
     e2e = None
     if not args.no_e2e:
         fh = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_F)).pin_memory()
-        uh = torch.zeros(n_total, dtype=torch.float64).pin_memory()
         ke = max(1, min(args.steps, 2))
+        uhs = [torch.zeros(n_total, dtype=torch.float64).pin_memory() for _ in range(ke)]   # u0 = 0 per step
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         e_upd = 0
-        for _ in range(ke):
-            uh.zero_()
+        for uh in uhs:
             rel, cycles = step(fh, uh)
             e_upd += updates(cycles)
         torch.cuda.synchronize()
@@ -515,19 +518,19 @@ def run_variants(args):
             "rtol": 1e-8, "variants": out}
 
 
-DISC_MESHES = {60: (0, 1), 480: (1, 2), 3840: (2, 4)}   # macro cells: (surface refinements, radial layers)
+DISC_MESHES = {60: (0, 1), 480: (1, 2), 3840: (2, 4), 30720: (3, 8)}   # cells: (surface refinements, layers)
 DISC_VARIANTS = ("fem", "lsqp_q1", "lsqp_q2", "lsqp_q3", "ipoly", "lsqp_dd", "ipoly_dd", "cons", "cons_dd")
 
 
 def run_discretisation(args):
     """The accuracy study of Sec. 4 (Table 4.1 and the DD / CONS comparison
-    of Sec. 4.2) on the GPU: for the 60-, 480- and 3840-cell shells
+    of Sec. 4.2) on the GPU: for the 60-, 480-, 3840- and 30720-cell shells
     (r in [0.55, 1]) and levels L = 2.. (N = 2^(L+2)) up to --disc-max-nodes,
     the exact solution u of Sec. 4 and f = -Laplace(u) at the nodes, the
     vertex-quadrature load vector (hhg_load_vector), 10 V(3,3) cycles from
     u = 0 per variant, and e = h^(3/2) ||I(u) - v||_2 over all nodes with
-    h = H/N and the macro mesh size H = 1, 1/2, 1/4 for the 60-, 480- and
-    3840-cell shells (each macro refinement halves it).  Variants: FEM (exact operator), LSQP q = 1, 2, 3, IPOLY, LSQP DD
+    h = H/N and the macro mesh size H = 1 for the 60-cell shell, halved by
+    each macro refinement.  Variants: FEM (exact operator), LSQP q = 1, 2, 3, IPOLY, LSQP DD
     and IPOLY DD (surrogate relaxation, exact residuals), CONS (the operator
     of the unprojected domain, compared with u at its own nodes) and CONS DD
     (relaxation with the unprojected stencils in the cell interiors).  dev =
@@ -540,8 +543,9 @@ def run_discretisation(args):
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)
     rows = []
-    for cells, (tang, layers) in DISC_MESHES.items():
-        for Lp in range(2, 7):
+    for cells in [int(c) for c in args.disc_cells.split(",")]:
+        tang, layers = DISC_MESHES[cells]
+        for Lp in range(args.disc_min_level, 7):
             N = 2 ** (Lp + 2)
             n_total, _ = hhg.hhg_problem_nodes(r1, r2, tang, layers, Lp + 2)
             if n_total > args.disc_max_nodes:
@@ -584,7 +588,7 @@ def run_discretisation(args):
             rows.append(row)
             print(json.dumps({"cells": cells, "L": Lp, "e": row["e"]}), file=sys.stderr, flush=True)
     return {"mode": "discretisation", "radii": [r1, r2], "cycles": "10 x V(3,3) from u = 0",
-            "h": "H/N, H = 1, 1/2, 1/4 for 60, 480, 3840 cells",
+            "h": "H/N, H = 1, 1/2, 1/4, 1/8 for 60, 480, 3840, 30720 cells",
             "load_vector": "vertex quadrature (hhg_load_vector)", "rows": rows}
 
 
