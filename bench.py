@@ -77,6 +77,8 @@ def parse():
                    help="f64: FP64 V-cycles; mixed: FP32 V-cycles inside FP64 iterative refinement")
     p.add_argument("--serve-requests", type=int, default=48,
                    help="requests of the serving stream reported beside the solve (0 = skip)")
+    p.add_argument("--serve-batch-rhs", type=int, default=16,
+                   help="continuous batching of the serving stream: right-hand sides per merged solve (1 = off)")
     p.add_argument("--disc-max-nodes", type=float, default=25e6,
                    help="--mode discretisation: largest level (total nodes) of the study")
     p.add_argument("--disc-cells", type=str, default="60,480,3840,30720",
@@ -410,14 +412,16 @@ SERVE_RADII = [0.35 + 0.05 * k for k in range(8)]   # inner radii of the request
 SERVE_LEVELS = [4, 5, 6, 7]                          # N = 16 .. 128 on the 60-macro shell
 
 
-def serve_run(n_requests, rate_hz=200.0, seed=2024, max_inflight=4, warm=True):
+def serve_run(n_requests, rate_hz=200.0, seed=2024, max_inflight=4, warm=True, max_batch_rhs=16):
     """Poisson stream of shell solves through the library's request loop
     (hhg_server_*): levels 4-7 and inner radius (from an 8-point grid in
     [0.35, 0.7]) drawn uniformly, 1-8 right-hand sides uniform[-1, 1] each,
     mixed precision to relative residual 1e-8.  With warm=True every
     (radius, level) hierarchy is built once before the timed stream, so the
-    stream measures the resident-hierarchy steady state.  Returns latency
-    percentiles and throughput from the library's own per-request stamps."""
+    stream measures the resident-hierarchy steady state.  max_batch_rhs > 1
+    turns on continuous batching (queued requests of one key merged into one
+    batched solve).  Returns latency percentiles and throughput from the
+    library's own per-request stamps."""
     import paper_1608_06473_gb300 as hhg
     import synthetic
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -432,7 +436,7 @@ def serve_run(n_requests, rate_hz=200.0, seed=2024, max_inflight=4, warm=True):
             pool[L] = np.stack([synthetic.uniform(n, 900 + b) for b in range(8)])
         return pool[L][:nr]
 
-    srv = hhg.Server(max_inflight=max_inflight, dtype=hhg.HHG_F32, rtol=1e-8)
+    srv = hhg.Server(max_inflight=max_inflight, dtype=hhg.HHG_F32, rtol=1e-8, max_batch_rhs=max_batch_rhs)
     try:
         if warm:
             ts = [srv.submit(rhs(ri, L, 1), r_inner=ri, L=L) for ri in SERVE_RADII for L in SERVE_LEVELS]
@@ -464,6 +468,9 @@ def serve_run(n_requests, rate_hz=200.0, seed=2024, max_inflight=4, warm=True):
             "mean_latency_s": float(lat.mean()), "throughput_req_s": n_requests / span,
             "throughput_rhs_s": n_rhs / span, "worst_relres": worst,
             "reused": int(sum(i["reused"] for i in infos)), "resident_hierarchies": stats["resident"],
+            "max_batch_rhs": max_batch_rhs,
+            "merged_requests": int(sum(i["batch_rhs"] > nr for i, (_, _, nr) in zip(infos, reqs))),
+            "mean_batch_rhs": float(np.mean([i["batch_rhs"] for i in infos])),
             "resident_gb": stats["bytes"] / 1e9,
             "workload": "Poisson arrivals (mean %g req/s) of shell solves on the 60-macro icosahedral shell, "
                         "levels 4-7 (N=16..128) and r_inner in {0.35,0.40,...,0.70} drawn uniformly, 1-8 "
@@ -635,7 +642,7 @@ def main():
         print(json.dumps(run_smoother(args)))
         return
     if args.mode == "serve":
-        print(json.dumps(serve_run(args.serve_requests)))
+        print(json.dumps(serve_run(args.serve_requests, max_batch_rhs=args.serve_batch_rhs)))
         return
     if args.mode == "variants":
         print(json.dumps(run_variants(args)))
@@ -653,7 +660,7 @@ def main():
     rank, world, local = dist_init(args.gpus)
     out = run_ours(args, rank, world, local)
     if rank == 0 and world == 1 and args.serve_requests > 0:
-        out["serving"] = serve_run(args.serve_requests)
+        out["serving"] = serve_run(args.serve_requests, max_batch_rhs=args.serve_batch_rhs)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.workload)

@@ -251,7 +251,16 @@ hhg_status hhg_set_graphs(hhg_shell* shell, int enable);
  * to the server's tolerance; its result does not depend on what else is in
  * flight (every kernel and reduction has a fixed order; only the FP32
  * smoother configuration, chosen per hierarchy by timing, may change the
- * rounding of mixed-precision solves). */
+ * rounding of mixed-precision solves).
+ *
+ * Continuous batching (max_batch_rhs > 1): when a slot takes a request, the
+ * requests queued behind it for the same geometry and level join it, up to
+ * max_batch_rhs right-hand sides in total, and run as one batched solve on
+ * one hierarchy (the weights of every node are evaluated once for all of
+ * them).  Every right-hand side is then stopped on its own: its iterate is
+ * taken at the first cycle where its relative residual meets rtol, so a
+ * request's result equals that of the same request solved alone with the
+ * same setting (to the batched kernels' rounding, 1e-10 relative in FP64). */
 typedef struct hhg_server hhg_server;
 
 typedef struct {
@@ -262,6 +271,7 @@ typedef struct {
   int max_cycles;
   double rtol;              /* stop at ||r|| <= rtol ||r0|| for every right-hand side */
   hhg_dtype dtype;          /* HHG_F64 or HHG_F32 (mixed precision, see hhg_vcycle) */
+  int max_batch_rhs;        /* continuous batching: right-hand sides per merged solve; 0 or 1 = off */
 } hhg_server_desc;
 
 /* One request's geometry and level (as hhg_shell_desc; L = fine_log2_intervals). */
@@ -273,9 +283,10 @@ typedef struct {
 /* Per-request record: times in seconds since the server was created. */
 typedef struct {
   double t_submit, t_start, t_end;
-  int cycles;               /* V-cycles run */
+  int cycles;               /* V-cycles run (with continuous batching: until its last right-hand side stopped) */
   int reused;               /* 1 if a resident hierarchy served it, 0 if one was built */
   hhg_status status;
+  int batch_rhs;            /* right-hand sides of the solve it ran in (its own, plus merged requests') */
 } hhg_request_info;
 
 /* Vector length and unknown count of a problem (no GPU work). */

@@ -55,7 +55,7 @@ class hhg_shell_desc(ctypes.Structure):
 class hhg_server_desc(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int), ("q", ctypes.c_int),
                 ("j", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_cycles", ctypes.c_int),
-                ("rtol", ctypes.c_double), ("dtype", ctypes.c_int)]
+                ("rtol", ctypes.c_double), ("dtype", ctypes.c_int), ("max_batch_rhs", ctypes.c_int)]
 
 
 class hhg_problem(ctypes.Structure):
@@ -65,7 +65,8 @@ class hhg_problem(ctypes.Structure):
 
 class hhg_request_info(ctypes.Structure):
     _fields_ = [("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_end", ctypes.c_double),
-                ("cycles", ctypes.c_int), ("reused", ctypes.c_int), ("status", ctypes.c_int)]
+                ("cycles", ctypes.c_int), ("reused", ctypes.c_int), ("status", ctypes.c_int),
+                ("batch_rhs", ctypes.c_int)]
 
 
 _lib = None
@@ -389,8 +390,8 @@ class Server:
     copied), wait() returns (u, relres, info) once it is solved."""
 
     def __init__(self, hbm_budget_bytes=0, max_inflight=4, q=2, j=2, nu1=3, nu2=3, max_cycles=60, rtol=1e-8,
-                 dtype=HHG_F32):
-        d = hhg_server_desc(hbm_budget_bytes, max_inflight, q, j, nu1, nu2, max_cycles, rtol, dtype)
+                 dtype=HHG_F32, max_batch_rhs=0):
+        d = hhg_server_desc(hbm_budget_bytes, max_inflight, q, j, nu1, nu2, max_cycles, rtol, dtype, max_batch_rhs)
         h = ctypes.c_void_p()
         _check(lib().hhg_server_create(ctypes.byref(d), ctypes.byref(h)))
         self.handle = h.value
@@ -414,7 +415,8 @@ class Server:
         if st != HHG_OK and raise_on_error:
             raise HHGError(st, hhg_last_error())
         return u, rel, {"t_submit": info.t_submit, "t_start": info.t_start, "t_end": info.t_end,
-                        "cycles": info.cycles, "reused": bool(info.reused), "status": info.status}
+                        "cycles": info.cycles, "reused": bool(info.reused), "status": info.status,
+                        "batch_rhs": info.batch_rhs}
 
     def stats(self):
         n, b, built = ctypes.c_int(), ctypes.c_size_t(), ctypes.c_int64()

@@ -1433,11 +1433,24 @@ static int solve_batch(hhg_shell* s, int op, int dtype, const double* f, double*
   op_residual(s, n, op, u, f, Lv.d_r, 10, st);
   std::vector<double> r0 = read_scalars(s, 10, st);
   std::vector<double> d0((size_t)nb, -1.0);
+  // per-right-hand-side stopping: copy a right-hand side's iterate out at the
+  // cycle where it first meets rtol (see hhg_shell::freeze_host)
+  const bool freeze = s->freeze_host != nullptr;
+  std::vector<char> frozen((size_t)nb, 0);
+  auto freeze_out = [&](int b, int c) {
+    launch_zero_list(Lv.d_dirichlet, Lv.n_dirichlet, u, nb, nt, st);
+    HHG_CUDA(cudaMemcpyAsync(s->freeze_host + (int64_t)b * nt, u + (int64_t)b * nt, sizeof(double) * nt,
+                             cudaMemcpyDeviceToHost, st));
+    HHG_CUDA(cudaStreamSynchronize(st));
+    s->freeze_cycle[b] = c;
+    frozen[b] = 1;
+  };
   bool todo = false;
   for (int b = 0; b < nb; ++b) {
     r0[b] = std::sqrt(r0[b]);
     HHG_CHECK(std::isfinite(r0[b]), HHG_EDIVERGED, "initial residual is not finite");
     rel[b] = r0[b] > 0 ? 1.0 : 0.0;
+    if (freeze && rel[b] <= rtol) freeze_out(b, 0);
     todo = todo || rel[b] > rtol;
   }
   if (dtype == HHG_F32) ensure_f32(s, st);
@@ -1513,6 +1526,7 @@ static int solve_batch(hhg_shell* s, int op, int dtype, const double* f, double*
     check_device_error(s, st);
     todo = false;
     for (int b = 0; b < nb; ++b) {
+      if (frozen[b]) continue;
       const double v = std::sqrt(rn[b]);
       HHG_CHECK(std::isfinite(v), HHG_EDIVERGED, "residual norm became NaN or Inf");
       if (dd) {
@@ -1521,11 +1535,15 @@ static int solve_batch(hhg_shell* s, int op, int dtype, const double* f, double*
       } else {
         rel[b] = r0[b] > 0 ? v / r0[b] : 0.0;
       }
+      if (freeze && rel[b] <= rtol) freeze_out(b, cyc + 1);
       todo = todo || rel[b] > rtol;
     }
     ++cyc;
   }
   launch_zero_list(Lv.d_dirichlet, Lv.n_dirichlet, u, nb, nt, st);
+  if (freeze)
+    for (int b = 0; b < nb; ++b)
+      if (!frozen[b]) freeze_out(b, cyc);  // not converged within max_cycles
   return cyc;
 }
 

@@ -1,8 +1,10 @@
 // Solve service over resident hierarchies (the hhg_server_* entry points of
 // include/hhg.h): a FIFO queue, admission by free slot and HBM budget, a
-// cache of built and fitted hierarchies keyed by geometry and level, and one
+// cache of built and fitted hierarchies keyed by geometry and level, one
 // host worker thread with its own CUDA stream per slot, so that admitted
-// requests overlap on the device.
+// requests overlap on the device, and optional continuous batching (queued
+// requests of one key merged into one batched solve, each right-hand side
+// stopped at its own convergence).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -96,14 +98,37 @@ int64_t free_nodes_of(const hhg_problem& p, int64_t* n_total) {
   return (nr - 1) * layer;
 }
 
+size_t vec_bytes_of(const Request* r) { return (size_t)2 * r->nrhs * r->n_total * sizeof(double); }
+
+// Continuous batching: the requests queued for the same key as the picked
+// one join its solve, in arrival order, while the right-hand sides fit
+// max_batch_rhs and their vectors the budget.
+void join_same_key(hhg_server* s, std::vector<Request*>* grp) {
+  if (s->d.max_batch_rhs <= 1) return;
+  const Key k = key_of((*grp)[0]->prob);
+  int rhs = (*grp)[0]->nrhs;
+  size_t bytes = vec_bytes_of((*grp)[0]);
+  for (auto it = s->pending.begin(); it != s->pending.end();) {
+    Request* r = *it;
+    if (key_of(r->prob) == k && rhs + r->nrhs <= s->d.max_batch_rhs && bytes + vec_bytes_of(r) <= s->free_budget()) {
+      grp->push_back(r);
+      rhs += r->nrhs;
+      bytes += vec_bytes_of(r);
+      it = s->pending.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
 // Picks the next admissible request under the lock: the first queued one
 // whose hierarchy is resident and idle, or for which a new hierarchy may be
-// built now.  Returns the request and the cache slot (-1 = build).
-bool pick(hhg_server* s, Request** req, int* slot) {
+// built now, together with the queued requests that join it.  Returns the
+// group and the cache slot (-1 = build).
+bool pick(hhg_server* s, std::vector<Request*>* grp, int* slot) {
   for (auto it = s->pending.begin(); it != s->pending.end(); ++it) {
     Request* r = *it;
-    const size_t vec_bytes = (size_t)2 * r->nrhs * r->n_total * sizeof(double);
-    if (vec_bytes > s->free_budget()) continue;
+    if (vec_bytes_of(r) > s->free_budget()) continue;
     const Key k = key_of(r->prob);
     int idle = -1;
     bool exists = false;
@@ -112,19 +137,14 @@ bool pick(hhg_server* s, Request** req, int* slot) {
         exists = true;
         if (!s->cache[c]->busy) idle = (int)c;
       }
-    if (idle >= 0) {
-      *req = r;
-      *slot = idle;
-      s->pending.erase(it);
-      return true;
-    }
-    if (exists && s->building) continue;  // wait for the resident one rather than build a copy
-    if (!s->building) {
-      *req = r;
-      *slot = -1;
-      s->pending.erase(it);
-      return true;
-    }
+    // while a hierarchy is being built, and (with continuous batching) while
+    // the key's hierarchy is busy, wait for it rather than build a copy
+    if (idle < 0 && (s->building || (exists && s->d.max_batch_rhs > 1))) continue;
+    grp->assign(1, r);
+    *slot = idle;
+    s->pending.erase(it);
+    join_same_key(s, grp);
+    return true;
   }
   return false;
 }
@@ -146,14 +166,19 @@ void evict_for(hhg_server* s, size_t need) {
   }
 }
 
-void run_request(hhg_server* s, Request* r, Resident& res, cudaStream_t st) {
-  const size_t n = (size_t)r->nrhs * r->n_total;
+// Solves a group of requests of one key as one batched V-cycle solve on the
+// resident hierarchy: right-hand sides in group order.  With continuous
+// batching each right-hand side is stopped on its own (hhg_shell::
+// freeze_host), so every request gets the iterate and relative residual of
+// the cycle where it met the tolerance.
+void run_group(hhg_server* s, const std::vector<Request*>& grp, Resident& res, cudaStream_t st) {
+  const int64_t nt = grp[0]->n_total;
+  int T = 0;
+  for (const Request* r : grp) T += r->nrhs;
+  const size_t n = (size_t)T * nt;
   hhg_shell* sh = res.shell;
   hhg_status status = HHG_OK;
-  auto fail = [&](hhg_status e, const char* what) {
-    status = e;
-    r->error = what;
-  };
+  std::string error;
   if (n > res.vec_cap) {
     if (res.df) cudaFreeAsync(res.df, st);
     if (res.du) cudaFreeAsync(res.du, st);
@@ -170,21 +195,65 @@ void run_request(hhg_server* s, Request* r, Resident& res, cudaStream_t st) {
   }
   double* df = res.df;
   double* du = res.du;
+  const bool merge = s->d.max_batch_rhs > 1;
+  std::vector<double> rel((size_t)T, 0.0), uh;
+  std::vector<int> fc((size_t)T, 0);
+  int cycles = 0;
   if (!df || !du) {
-    fail(HHG_ENOMEM, "request vectors do not fit on the device");
+    status = HHG_ENOMEM;
+    error = "request vectors do not fit on the device";
   } else {
-    cudaMemcpyAsync(df, r->f.data(), n * sizeof(double), cudaMemcpyHostToDevice, st);
+    size_t o = 0;
+    for (const Request* r : grp) {
+      cudaMemcpyAsync(df + o, r->f.data(), r->f.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+      o += r->f.size();
+    }
     cudaMemsetAsync(du, 0, n * sizeof(double), st);
-    int cycles = 0;
-    status = hhg_vcycle(sh, HHG_OP_LSQP, s->d.dtype, df, du, s->d.nu1, s->d.nu2, s->d.max_cycles, s->d.rtol,
-                        r->nrhs, r->relres.data(), &cycles, st);
-    if (status != HHG_OK) r->error = hhg_last_error();
-    r->info.cycles = cycles;
-    if (cudaMemcpyAsync(r->u.data(), du, n * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-      fail(HHG_ECUDA, "copy of the solution failed");
+    if (merge) {
+      uh.resize(n);
+      sh->freeze_host = uh.data();
+      sh->freeze_cycle = fc.data();
+    }
+    status = hhg_vcycle(sh, HHG_OP_LSQP, s->d.dtype, df, du, s->d.nu1, s->d.nu2, s->d.max_cycles, s->d.rtol, T,
+                        rel.data(), &cycles, st);
+    sh->freeze_host = nullptr;
+    sh->freeze_cycle = nullptr;
+    if (status != HHG_OK) error = hhg_last_error();
+    if (!merge && cudaMemcpyAsync(grp[0]->u.data(), du, n * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess &&
+        status == HHG_OK) {
+      status = HHG_ECUDA;
+      error = "copy of the solution failed";
+    }
   }
-  if (cudaStreamSynchronize(st) != cudaSuccess && status == HHG_OK) fail(HHG_ECUDA, "stream failed");
-  r->info.status = status;
+  if (cudaStreamSynchronize(st) != cudaSuccess && status == HHG_OK) {
+    status = HHG_ECUDA;
+    error = "stream failed";
+  }
+  size_t o = 0;
+  int b0 = 0;
+  for (Request* r : grp) {
+    hhg_status rs = status;
+    int rc = cycles;
+    bool conv = true;
+    if (merge) {
+      rc = 0;
+      for (int b = 0; b < r->nrhs; ++b) rc = std::max(rc, fc[(size_t)b0 + b]);
+      if (!uh.empty()) std::memcpy(r->u.data(), uh.data() + o, r->u.size() * sizeof(double));
+    }
+    for (int b = 0; b < r->nrhs; ++b) {
+      r->relres[(size_t)b] = rel[(size_t)b0 + b];
+      conv = conv && rel[(size_t)b0 + b] <= s->d.rtol;
+    }
+    // a merged solve that did not converge fails only the requests whose
+    // own right-hand sides missed the tolerance
+    if (rs == HHG_ENOCONV && conv) rs = HHG_OK;
+    r->info.status = rs;
+    r->info.cycles = rc;
+    r->info.batch_rhs = T;
+    r->error = rs == HHG_OK ? std::string() : error;
+    o += r->u.size();
+    b0 += r->nrhs;
+  }
 }
 
 void worker(hhg_server* s) {
@@ -192,26 +261,30 @@ void worker(hhg_server* s) {
   cudaStream_t st = nullptr;
   cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   for (;;) {
-    Request* r = nullptr;
+    std::vector<Request*> grp;
     int slot = -1;
     size_t vec_bytes = 0;
     hhg_shell* sh_cached = nullptr;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv_work.wait(lk, [&] { return (s->stop && s->pending.empty()) || pick(s, &r, &slot); });
-      if (!r) break;
-      vec_bytes = (size_t)2 * r->nrhs * r->n_total * sizeof(double);
+      s->cv_work.wait(lk, [&] { return (s->stop && s->pending.empty()) || pick(s, &grp, &slot); });
+      if (grp.empty()) break;
+      for (const Request* q : grp) vec_bytes += vec_bytes_of(q);
       s->used += vec_bytes;
       ++s->active;
       if (slot >= 0) {
         s->cache[slot]->busy = true;
         sh_cached = s->cache[slot]->shell;
-        r->info.reused = 1;
       } else {
         s->building = true;
       }
-      r->info.t_start = s->now();
+      const double t = s->now();
+      for (Request* q : grp) {
+        q->info.reused = slot >= 0 ? 1 : 0;
+        q->info.t_start = t;
+      }
     }
+    Request* r = grp[0];
     hhg_shell* sh = nullptr;
     if (slot >= 0) {
       sh = sh_cached;
@@ -249,8 +322,10 @@ void worker(hhg_server* s) {
       s->building = false;
       s->cv_work.notify_all();
       if (!sh) {
-        r->info.status = st_build;
-        r->error = err;
+        for (Request* q : grp) {
+          q->info.status = st_build;
+          q->error = err;
+        }
       } else {
         auto res = std::make_unique<Resident>();
         res->key = key_of(r->prob);
@@ -269,18 +344,21 @@ void worker(hhg_server* s) {
         for (auto& c : s->cache)
           if (c->shell == sh) res = c.get();
       }
-      run_request(s, r, *res, st);
+      run_group(s, grp, *res, st);
     }
     {
       std::lock_guard<std::mutex> lk(s->mu);
-      r->info.t_end = s->now();
-      r->done = true;
+      const double t = s->now();
+      for (Request* q : grp) {
+        q->info.t_end = t;
+        q->done = true;
+      }
       s->used -= vec_bytes;
       --s->active;
       for (auto& c : s->cache)
         if (c->shell == sh) {
           c->busy = false;
-          c->last_used = r->info.t_end;
+          c->last_used = t;
           // a hierarchy may have grown (FP32 buffers, batch capacity)
           s->used += sh->alloc.used - c->bytes;
           c->bytes = sh->alloc.used;
@@ -311,7 +389,7 @@ hhg_status hhg_problem_nodes(const hhg_problem* p, int64_t* n_total, int64_t* n_
 
 hhg_status hhg_server_create(const hhg_server_desc* d, hhg_server** out) {
   if (!d || !out || d->max_inflight < 1 || d->max_inflight > 64 || d->q < 1 || d->q > 3 || d->j < 1 ||
-      d->rtol < 0 || d->max_cycles < 1 || (d->dtype != HHG_F64 && d->dtype != HHG_F32)) {
+      d->rtol < 0 || d->max_cycles < 1 || (d->dtype != HHG_F64 && d->dtype != HHG_F32) || d->max_batch_rhs < 0) {
     set_error("invalid server descriptor");
     return HHG_EINVAL;
   }

@@ -181,6 +181,13 @@ struct hhg_shell {
   double* d_cg = nullptr;              // coarse-solver vectors
   double* d_uprev = nullptr;           // previous iterate of double-discretisation cycles
   int64_t uprev_len = 0;
+  // per-right-hand-side stopping (continuous batching of the solve server):
+  // when set, each right-hand side's iterate is copied to freeze_host + b *
+  // n_total at the first cycle where it meets rtol (its cycle count to
+  // freeze_cycle[b]), it no longer keeps the cycle loop going, and its
+  // relative residual stays the one of that cycle
+  double* freeze_host = nullptr;
+  int* freeze_cycle = nullptr;
   int* d_err = nullptr;                // device error word of the staged kernels (0 = ok)
   // batches: work vectors, halo copies, step buffers, reduction and coarse
   // solver scratch hold `cap` right-hand sides; `nb` of them are active in

@@ -74,3 +74,27 @@ def test_request_that_cannot_fit_fails():
         with pytest.raises(hhg.HHGError) as e:
             srv.wait(t)
         assert e.value.status == hhg.Status.ENOMEM
+
+
+@pytest.mark.parametrize("dtype,tol", [(hhg.HHG_F64, 1e-10), (hhg.HHG_F32, 1e-6)])
+def test_continuous_batching_equals_alone(dtype, tol):
+    """Continuous batching (max_batch_rhs): requests of one key queued while
+    its hierarchy is busy are merged into one batched solve, and every
+    right-hand side is stopped at its own convergence, so each request gets
+    the result and cycle count of the same request solved alone with the same
+    setting (to the batched kernels' rounding: 1e-10 in FP64, the
+    mixed-precision bar in FP32)."""
+    ri, L = 0.55, 4
+    fs = [rhs(200 + k, ri, L, nr) for k, nr in enumerate([1, 2, 1, 3, 1, 2])]
+    with hhg.Server(max_inflight=1, dtype=dtype, max_batch_rhs=8) as srv:
+        tickets = [srv.submit(f, r_inner=ri, L=L) for f in fs]
+        merged = [srv.wait(t) for t in tickets]
+    with hhg.Server(max_inflight=1, dtype=dtype, max_batch_rhs=8) as srv:
+        alone = [srv.wait(srv.submit(f, r_inner=ri, L=L)) for f in fs]
+    assert any(im["batch_rhs"] > len(f) for f, (_, _, im) in zip(fs, merged))
+    for f, (um, rm, im), (ua, ra, ia) in zip(fs, merged, alone):
+        assert ia["batch_rhs"] == len(f) and im["batch_rhs"] >= len(f)
+        assert np.all(rm <= 1e-8) and np.all(ra <= 1e-8)
+        if dtype == hhg.HHG_F64:
+            assert im["cycles"] == ia["cycles"]
+        assert rel(um, ua) <= tol
