@@ -526,7 +526,8 @@ def run_variants(args):
 
 
 DISC_MESHES = {60: (0, 1), 480: (1, 2), 3840: (2, 4), 30720: (3, 8)}   # cells: (surface refinements, layers)
-DISC_VARIANTS = ("fem", "lsqp_q1", "lsqp_q2", "lsqp_q3", "ipoly", "lsqp_dd", "ipoly_dd", "cons", "cons_dd")
+DISC_VARIANTS = ("fem", "lsqp_q1", "lsqp_q2", "lsqp_q3", "ipoly_q1", "ipoly", "ipoly_q3", "lsqp_dd", "ipoly_dd",
+                 "cons", "cons_dd")
 
 
 def run_discretisation(args):
@@ -537,7 +538,7 @@ def run_discretisation(args):
     vertex-quadrature load vector (hhg_load_vector), 10 V(3,3) cycles from
     u = 0 per variant, and e = h^(3/2) ||I(u) - v||_2 over all nodes with
     h = H/N and the macro mesh size H = 1 for the 60-cell shell, halved by
-    each macro refinement.  Variants: FEM (exact operator), LSQP q = 1, 2, 3, IPOLY, LSQP DD
+    each macro refinement.  Variants: FEM (exact operator), LSQP q = 1, 2, 3, IPOLY q = 1, 2, 3, LSQP DD
     and IPOLY DD (surrogate relaxation, exact residuals), CONS (the operator
     of the unprojected domain, compared with u at its own nodes) and CONS DD
     (relaxation with the unprojected stencils in the cell interiors).  dev =
@@ -570,13 +571,14 @@ def run_discretisation(args):
                 plan = ([("cons", hhg.HHG_OP_LSQP, ("lsqp", 2))] if unproj else
                         [("fem", hhg.HHG_OP_IFEM, None), ("lsqp_q1", hhg.HHG_OP_LSQP, ("lsqp", 1)),
                          ("lsqp_q2", hhg.HHG_OP_LSQP, ("lsqp", 2)), ("lsqp_q3", hhg.HHG_OP_LSQP, ("lsqp", 3)),
-                         ("lsqp_dd", hhg.HHG_OP_DD, ("lsqp", 2)), ("ipoly", hhg.HHG_OP_LSQP, ("ipoly", 2)),
+                         ("lsqp_dd", hhg.HHG_OP_DD, ("lsqp", 2)), ("ipoly_q1", hhg.HHG_OP_LSQP, ("ipoly", 1)),
+                         ("ipoly_q3", hhg.HHG_OP_LSQP, ("ipoly", 3)), ("ipoly", hhg.HHG_OP_LSQP, ("ipoly", 2)),
                          ("ipoly_dd", hhg.HHG_OP_DD, ("ipoly", 2)), ("cons_dd", hhg.HHG_OP_DD, ("cons", 2))])
                 for name, op, fit in plan:
                     if fit and fit[0] == "lsqp":
                         s.fit(fit[1], 2, stream=stream)
                     elif fit and fit[0] == "ipoly":
-                        s.fit_ipoly(stream=stream)
+                        s.fit_ipoly(fit[1], stream=stream)
                     elif fit:
                         s.fit_cons(fit[1], 2, stream=stream)
                     u.zero_()

@@ -162,6 +162,13 @@ hhg_status hhg_fit_surrogate(hhg_shell* shell, int q, int j, void* stream);
  * HHG_OP_DD then use these polynomials. */
 hhg_status hhg_fit_ipoly(hhg_shell* shell, void* stream);
 
+/* IPOLY of degree q in 1..3 (Sec. 3.1, Table 4.1): interpolation at the m_q
+ * nodes of degree q of the cell shrunk to its interior, (1,1,1) +
+ * (N-4)(a,b,c)/q for a+b+c <= q, each coordinate rounded to the nearest fine
+ * node where (N-4)/q is not an integer (q = 3 at N = 8, 32, 128).  q = 2 is
+ * hhg_fit_ipoly. */
+hhg_status hhg_fit_ipoly_degree(hhg_shell* shell, int q, void* stream);
+
 /* CONS stencils as the cell-interior surrogate (Sec. 4.1, "CONS DD"): the
  * polynomials of hhg_fit_surrogate fitted to the stencils of the unprojected
  * domain Omega_H (Phi = Id), which are constant per macro cell and so

@@ -91,17 +91,17 @@ def fit(level: M.Level, A: sp.csr_matrix, q: int = 2, j: int = 2, cells=None) ->
     return out
 
 
-def fit_ipoly(level: M.Level, A: sp.csr_matrix, cells=None) -> np.ndarray:
-    """IPOLY (Sec. 3.1): the quadratic polynomials interpolating the exact
-    off-centre weights at the ten points of ipoly_points (a square system,
-    solved like the least-squares one); shape (n_cells, 14, 10)."""
+def fit_ipoly(level: M.Level, A: sp.csr_matrix, cells=None, q: int = 2) -> np.ndarray:
+    """IPOLY (Sec. 3.1): the polynomials of degree q interpolating the exact
+    off-centre weights at the m_q points of ipoly_points (a square system,
+    solved like the least-squares one); shape (n_cells, 14, m_q)."""
     N = level.N
     assert level_index(N) >= 1
-    pts = ipoly_points(N)
+    pts = ipoly_points(N, q)
     cells = np.arange(level.shell.nC) if cells is None else np.asarray(cells)
-    out = np.empty((len(cells), 14, n_coeffs(2)))
+    out = np.empty((len(cells), 14, n_coeffs(q)))
     for n, c in enumerate(cells):
-        out[n] = fit_values(pts, N, 2, exact_weights_at(level, A, c, pts)[:, :14])
+        out[n] = fit_values(pts, N, q, exact_weights_at(level, A, c, pts)[:, :14])
     return out
 
 
@@ -155,9 +155,18 @@ def fit_errors(exact: np.ndarray, surrogate: np.ndarray):
     return np.sqrt(np.mean(d * d, axis=1)), np.max(np.abs(d), axis=1)
 
 
-def ipoly_points(N: int) -> np.ndarray:
-    """The ten IPOLY interpolation points of Sec. 3.1 for q = 2: the quadratic
-    nodes of the macro cell shrunk to its interior, a = N - 3, b = N/2 - 1."""
-    a, b = N - 3, N // 2 - 1
-    return np.array([(1, 1, 1), (1, 1, a), (1, a, 1), (a, 1, 1), (1, 1, b), (1, b, 1), (b, 1, 1),
-                     (1, b, b), (b, 1, b), (b, b, 1)], dtype=np.int64)
+def ipoly_points(N: int, q: int = 2) -> np.ndarray:
+    """The IPOLY interpolation points of Sec. 3.1: the nodes of degree q of
+    the macro cell shrunk to its interior (vertices (1,1,1), (N-3,1,1),
+    (1,N-3,1), (1,1,N-3)), i.e. (1,1,1) + (N-4) (a,b,c)/q for a+b+c <= q.
+    For q = 2 these are the ten points a = N - 3, b = N/2 - 1 listed below;
+    where (N-4)/q is not an integer (q = 3 and N = 8, 32, 128) each
+    coordinate is rounded to the nearest fine node (the paper states the
+    points for q = 2 only)."""
+    if q == 2:
+        a, b = N - 3, N // 2 - 1
+        return np.array([(1, 1, 1), (1, 1, a), (1, a, 1), (a, 1, 1), (1, 1, b), (1, b, 1), (b, 1, 1),
+                         (1, b, b), (b, 1, b), (b, b, 1)], dtype=np.int64)
+    node = lambda x: int(np.floor(1.0 + (N - 4) * x / q + 0.5))
+    return np.array([(node(a), node(b), node(c)) for a in range(q + 1) for b in range(q + 1 - a)
+                     for c in range(q + 1 - a - b)], dtype=np.int64)

@@ -250,7 +250,7 @@ class Hierarchy:
 def build_hierarchy(shell: M.Shell, N_fine: int, op: str = "lsqp", q: int = 2, j: int = 2,
                     mapped: bool = True):
     """Levels, operators and transfers for a shell: op = 'ifem' (exact),
-    'lsqp' or 'ipoly' (surrogate on N >= 8), 'dd-lsqp' / 'dd-ipoly' (double
+    'lsqp' or 'ipoly' (surrogate of degree q on N >= 8), 'dd-lsqp' / 'dd-ipoly' (double
     discretisation: surrogate sweeps, exact residuals) or 'dd-cons' (CONS DD
     of Sec. 4.1: sweeps whose cell-interior rows are the stencils of the
     unprojected domain, exact residuals).  mapped = False builds every level
@@ -265,8 +265,8 @@ def build_hierarchy(shell: M.Shell, N_fine: int, op: str = "lsqp", q: int = 2, j
         S = A
         kind = op.split("-")[-1]
         if kind in ("lsqp", "ipoly") and N >= 8:
-            coef = LS.fit(lv, A, q, j) if kind == "lsqp" else LS.fit_ipoly(lv, A)
-            S = LS.surrogate_operator(lv, A, coef, q if kind == "lsqp" else 2)
+            coef = LS.fit(lv, A, q, j) if kind == "lsqp" else LS.fit_ipoly(lv, A, q=q)
+            S = LS.surrogate_operator(lv, A, coef, q)
         elif kind == "cons" and N >= 8:
             lu = M.make_level(shell, N, mapped=False)
             S = LS.with_interior_stencils(lv, A, F.interior_stencils(lu, F.assemble(lu)))

@@ -83,6 +83,7 @@ _SIGS = {
     "hhg_fit_surrogate": [_P, _I, _I, _P],
     "hhg_fit_ipoly": [_P, _P],
     "hhg_fit_cons": [_P, _I, _I, _P],
+    "hhg_fit_ipoly_degree": [_P, _I, _P],
     "hhg_load_vector": [_P, _I, _P, _P, _P],
     "hhg_apply": [_P, _I, _I, _I, _P, _P, _I, _P],
     "hhg_residual": [_P, _I, _I, _I, _P, _P, _P, _I, _P, _P],
@@ -256,6 +257,10 @@ def hhg_fit_ipoly(shell: int, stream=None):
     _check(lib().hhg_fit_ipoly(shell, _stream(stream)))
 
 
+def hhg_fit_ipoly_degree(shell: int, q: int = 2, stream=None):
+    _check(lib().hhg_fit_ipoly_degree(shell, q, _stream(stream)))
+
+
 def hhg_fit_cons(shell: int, q: int = 2, j: int = 2, stream=None):
     _check(lib().hhg_fit_cons(shell, q, j, _stream(stream)))
 
@@ -353,8 +358,11 @@ class Shell:
     def fit(self, q=2, j=2, stream=None):
         hhg_fit_surrogate(self.handle, q, j, stream)
 
-    def fit_ipoly(self, stream=None):
-        hhg_fit_ipoly(self.handle, stream)
+    def fit_ipoly(self, q=2, stream=None):
+        if q == 2:
+            hhg_fit_ipoly(self.handle, stream)
+        else:
+            hhg_fit_ipoly_degree(self.handle, q, stream)
 
     def fit_cons(self, q=2, j=2, stream=None):
         hhg_fit_cons(self.handle, q, j, stream)

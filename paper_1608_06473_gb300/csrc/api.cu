@@ -798,9 +798,9 @@ static void vcycle_rec32(hhg_shell* s, int n, int op, const float* f, float* u, 
 // ---------------------------------------------------------------------------
 
 // ipoly = false: LSQP on S_l = M_{m(l,j)} (Sec. 3.2); ipoly = true: IPOLY
-// (Sec. 3.1), q = 2 interpolation at the ten quadratic nodes of the macro
-// cell shrunk to its interior, a = N - 3, b = N/2 - 1 (the square system is
-// solved by the same QR).  unprojected = true samples the stencils of the
+// (Sec. 3.1), interpolation at the m_q nodes of degree q of the macro cell
+// shrunk to its interior (for q = 2 the ten points a = N - 3, b = N/2 - 1;
+// the square system is solved by the same QR).  unprojected = true samples the stencils of the
 // unprojected domain (Phi = Id; constant per cell, so every degree
 // reproduces them): the cell-interior rows of the CONS operator (Sec. 4.1).
 static void fit(hhg_shell* s, int q, int j, cudaStream_t st, bool ipoly = false, bool unprojected = false) {
@@ -822,11 +822,19 @@ static void fit(hhg_shell* s, int q, int j, cudaStream_t st, bool ipoly = false,
     if (N < 8) continue;
     const int l = (int)n;  // paper level: N = 2^(l+2)
     std::vector<uint32_t> pts;
-    if (ipoly) {
+    if (ipoly && q == 2) {
       const int a = N - 3, b = N / 2 - 1;
       const int P[10][3] = {{1, 1, 1}, {1, 1, a}, {1, a, 1}, {a, 1, 1}, {1, 1, b},
                             {1, b, 1}, {b, 1, 1}, {1, b, b}, {b, 1, b}, {b, b, 1}};
       for (auto& p : P) pts.push_back(pack_ijk(p[0], p[1], p[2]));
+    } else if (ipoly) {
+      // the nodes of degree q of the shrunk cell, (1,1,1) + (N-4)(a,b,c)/q,
+      // each coordinate rounded to the nearest fine node where (N-4)/q is
+      // not an integer
+      auto node = [&](int x) { return (int)std::floor(1.0 + (double)(N - 4) * x / q + 0.5); };
+      for (int a = 0; a <= q; ++a)
+        for (int b = 0; b <= q - a; ++b)
+          for (int c = 0; c <= q - a - b; ++c) pts.push_back(pack_ijk(node(a), node(b), node(c)));
     } else {
       const int mlev = std::min(l, std::max(1, j));
       const int Nm = 4 << mlev, scale = 1 << (l - mlev);
@@ -1187,6 +1195,14 @@ hhg_status hhg_fit_ipoly(hhg_shell* s, void* stream) {
   return guarded([&] {
     HHG_CHECK(s != nullptr, HHG_EINVAL, "NULL shell");
     fit(s, 2, 0, (cudaStream_t)stream, true);
+  });
+}
+
+hhg_status hhg_fit_ipoly_degree(hhg_shell* s, int q, void* stream) {
+  return guarded([&] {
+    HHG_CHECK(s != nullptr, HHG_EINVAL, "NULL shell");
+    HHG_CHECK(q >= 1 && q <= 3, HHG_EINVAL, "q must be 1, 2 or 3");
+    fit(s, q, 0, (cudaStream_t)stream, true);
   });
 }
 

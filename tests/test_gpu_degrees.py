@@ -1,8 +1,9 @@
 """LSQP surrogates of degree q = 1 and 3 and sampling sets j = 1 and 3
-(Sec. 3.2, S_l = M_{m(l,j)}) on the GPU against the FP64 oracle: FP64 apply
-and one smoother sweep to 1e-12 relative, FP32 apply to 2e-5 relative (the
-FP32 bar of the q = 2 tests), on the 60-cell shell at N = 8 and 16, and at
-N = 32 for j = 3 (the first level where m(l, 3) differs from m(l, 2))."""
+(Sec. 3.2, S_l = M_{m(l,j)}), and IPOLY of degree 1 and 3 (Sec. 3.1), on the
+GPU against the FP64 oracle: FP64 apply and one smoother sweep to 1e-12
+relative, FP32 apply to 2e-5 relative (the FP32 bar of the q = 2 tests), on
+the 60-cell shell at N = 8 and 16, and at N = 32 for j = 3 (the first level
+where m(l, 3) differs from m(l, 2))."""
 import numpy as np
 import pytest
 
@@ -59,3 +60,24 @@ def test_degree_and_sampling(setup, q, j, L):
         assert rel(y.cpu().numpy(), op.apply(u), lv.free) <= 1e-12
         assert rel(us.cpu().numpy(), op.sweep(op.mask * u, f), lv.free) <= 1e-12
         assert rel(y32.cpu().numpy().astype(np.float64), op.apply(u32.astype(np.float64)), lv.free) <= TOL32
+
+
+@pytest.mark.parametrize("q", [1, 3])
+def test_ipoly_degree(setup, q):
+    """IPOLY of degree 1 and 3 (hhg_fit_ipoly_degree): FP64 apply and one
+    sweep against the oracle's IPOLY surrogate at N = 8 and 16 to 1e-12."""
+    levels, As, s4, _ = setup
+    s4.fit_ipoly(q)
+    for l2 in (3, 4):
+        lv, A = levels[l2], As[l2]
+        op = mg.Operator(lv, LS.surrogate_operator(lv, A, LS.fit_ipoly(lv, A, q=q), q))
+        u = synthetic.uniform(lv.n_total, synthetic.SEED_U)
+        f = synthetic.uniform(lv.n_total, synthetic.SEED_F)
+        ut, ft = torch.from_numpy(u).cuda(), torch.from_numpy(f).cuda()
+        y = torch.empty_like(ut)
+        s4.apply(ut, y, L=l2, op=hhg.HHG_OP_LSQP)
+        us = ut.clone()
+        s4.smooth(ft, us, 1, L=l2, op=hhg.HHG_OP_LSQP)
+        torch.cuda.synchronize()
+        assert rel(y.cpu().numpy(), op.apply(u), lv.free) <= 1e-12
+        assert rel(us.cpu().numpy(), op.sweep(op.mask * u, f), lv.free) <= 1e-12

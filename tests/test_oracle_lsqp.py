@@ -161,3 +161,43 @@ def test_non_symmetry_is_first_order():
         out.append(sp.linalg.norm(B - B.T) / sp.linalg.norm(E))
     assert out[0] > out[1] > out[2]
     assert 1.5 <= out[1] / out[2] <= 2.5
+
+
+def test_ipoly_points_of_degree_q():
+    """Sec. 3.1's points generalised to degree q: the m_q nodes of degree q of
+    the shrunk cell (1,1,1), (N-3,1,1), (1,N-3,1), (1,1,N-3); q = 1 gives its
+    vertices, q = 2 the ten listed points, q = 3 at N = 16 and 64 the exact
+    lattice (1,1,1) + (N-4)/3 (a,b,c); elsewhere rounded, still distinct
+    interior points with a nonsingular interpolation matrix."""
+    for N in (8, 16, 32, 64, 128, 256):
+        for q in (1, 2, 3):
+            P = LS.ipoly_points(N, q)
+            assert len(P) == LS.n_coeffs(q) == len({tuple(p) for p in P})
+            assert np.all(P >= 1) and np.all(P.sum(axis=1) <= N - 1)
+            assert np.linalg.matrix_rank(LS.design_matrix(P, N, q)) == LS.n_coeffs(q)
+        v = {(1, 1, 1), (N - 3, 1, 1), (1, N - 3, 1), (1, 1, N - 3)}
+        assert {tuple(p) for p in LS.ipoly_points(N, 1)} == v
+        assert v <= {tuple(p) for p in LS.ipoly_points(N, 3)}
+    for N in (16, 64):
+        h = (N - 4) // 3
+        lattice = {(1 + h * a, 1 + h * b, 1 + h * c) for a in range(4) for b in range(4 - a) for c in range(4 - a - b)}
+        assert {tuple(p) for p in LS.ipoly_points(N, 3)} == lattice
+
+
+@pytest.mark.parametrize("q", [1, 3])
+def test_ipoly_of_degree_q_interpolates_and_recovers_polynomials(q):
+    """IPOLY of degree q reproduces weights that are polynomials of degree q
+    exactly, and interpolates the exact stencils at its points."""
+    rng = np.random.default_rng(31 + q)
+    N = 32
+    P = LS.ipoly_points(N, q)
+    true = rng.normal(size=(14, LS.n_coeffs(q)))
+    vals = LS.evaluate(true[None], P, N, q)[0][:, :14]
+    got = LS.fit_values(P, N, q, vals)
+    allp = M.interior_points(N)
+    assert np.allclose(LS.evaluate(got[None], allp, N, q), LS.evaluate(true[None], allp, N, q),
+                       rtol=0, atol=1e-10 * np.abs(true).max())
+    sh = M.make_shell()
+    ex = LO.exact_stencils(sh, N, 5, P)[:, :14]
+    cip = LS.fit_values(P, N, q, ex)
+    assert np.allclose(LS.evaluate(cip[None], P, N, q)[0][:, :14], ex, rtol=0, atol=1e-12 * np.abs(ex).max())
