@@ -168,6 +168,23 @@ def test_dd_with_equal_operators_is_the_plain_cycle():
     assert np.array_equal(a, b)
 
 
+def test_cons_dd_on_the_unprojected_domain_is_the_plain_cycle():
+    """CONS DD relaxes with the stencils of the unprojected domain in the cell
+    interiors; on an unprojected shell those are the exact operator's own
+    rows, so its relaxation operator equals the exact one and the cycle is the
+    plain FEM cycle (to the rounding of re-reading the rows)."""
+    sh = M.make_shell()
+    Hc = mg.build_hierarchy(sh, 16, "dd-cons", mapped=False)
+    He = mg.build_hierarchy(sh, 16, "ifem", mapped=False)
+    for a, b in zip(Hc.smooth_ops, He.ops):
+        assert abs(a.A - b.A).max() <= 1e-14 * abs(b.A).max()
+    f = synthetic.uniform(He.levels[-1].n_total, synthetic.SEED_F)
+    u = np.zeros_like(f)
+    x = Hc.vcycle(len(Hc.ops) - 1, u, f)
+    y = He.vcycle(len(He.ops) - 1, u, f)
+    assert np.linalg.norm(x - y) <= 1e-12 * np.linalg.norm(y)
+
+
 def test_dd_recovers_the_exact_operator_solution():
     """Sec. 4.1: relaxing with the surrogate and computing residuals with the
     exact operator moves the iterate towards the exact operator's solution
