@@ -11,6 +11,8 @@ are checked on a seeded sample of cells this way.
 """
 from __future__ import annotations
 
+import functools
+
 import numpy as np
 import scipy.sparse as sp
 
@@ -21,6 +23,12 @@ from . import mesh as M
 
 def _offsets(sh: M.Shell, N: int):
     return M._prim_offsets(sh, N)
+
+
+@functools.lru_cache(maxsize=8)
+def _tet_nodes(N: int) -> np.ndarray:
+    """fem.cell_tet_nodes(N), computed once per N (the same for every cell)."""
+    return F.cell_tet_nodes(N)
 
 
 def cell_map(sh: M.Shell, N: int, c: int) -> np.ndarray:
@@ -40,7 +48,7 @@ def cell_coords(sh: M.Shell, N: int, c: int) -> np.ndarray:
 def cell_matrix(sh: M.Shell, N: int, c: int) -> sp.csr_matrix:
     """Sum of the element matrices of cell c's tetrahedra, in cell-local
     (lin_full) numbering; its interior rows are rows of L_l."""
-    loc = F.cell_tet_nodes(N)
+    loc = _tet_nodes(N)
     X = cell_coords(sh, N, c)
     K = F.element_stiffness(X[loc])
     n = M.tet_count(N)
