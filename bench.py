@@ -50,9 +50,35 @@ WORKLOADS = {
                               "r in [0.55, 1]"),
     "shell60_N16": (0, 1, 4, "60 macro cells (icosahedral shell, 1 layer), N=16, r in [0.55, 1]"),
 }
-HBM_MEASURED_GBS = 6794.8    # MEASURED_PEAKS.json: copy bandwidth on the GB300s
-FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (recipe's nominal figure: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)
+HBM_FALLBACK_GBS = 6800.0    # profiling recipe's fallback, used only when MEASURED_PEAKS.json is absent
 LSQP_FLOPS = {1: 44, 2: 59, 3: 74}   # Table 4.2: 29 + 15 q flops per stencil-based update
+# FP64 flops of Eq. 5.1 once the weights are known (Table 4.2's CONS count:
+# 14 multiply-adds and the division by the centre weight, here a multiply
+# by its reciprocal).  The LSQP kernels issue exactly these on the FP64 pipe;
+# the 15 q flops of the weight recurrence run in exact integer arithmetic.
+STENCIL_FLOPS = 29
+
+
+def hbm_peak():
+    """(GB/s, note): MEASURED_PEAKS.json's copy bandwidth, else the recipe's fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            return float(json.load(open(path))["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs, copy)"
+        except (KeyError, ValueError):
+            pass
+    return HBM_FALLBACK_GBS, "of fallback (profiling recipe, no MEASURED_PEAKS.json)"
+
+
+def measure_peaks(hhg, stream=None):
+    """FP64 and FP32 multiply-add throughput of this GPU now (hhg_peak_rate:
+    independent FMA chains on every SM, best of three ~150 ms runs)."""
+    out = {}
+    for name, kind in (("fp64_fma_per_s", hhg.PEAK_FP64_FMA), ("fp32_fma_per_s", hhg.PEAK_FP32_FMA)):
+        out[name] = hhg.hhg_peak_rate(kind, stream)[0]
+    out["fp64_tflops"] = 2 * out["fp64_fma_per_s"] / 1e12
+    out["fp32_tflops"] = 2 * out["fp32_fma_per_s"] / 1e12
+    return out
 
 
 def parse():
@@ -66,7 +92,8 @@ def parse():
     p.add_argument("--j", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--mode", choices=["solve", "smoother", "serve", "variants", "discretisation"], default="solve",
+    p.add_argument("--mode", choices=["solve", "smoother", "serve", "variants", "discretisation", "batch", "peaks"],
+                   default="solve",
                    help="solve: the whole path per step (default); smoother: finest-level sweeps only "
                         "(for profiling the smoother kernels)")
     p.add_argument("--op", choices=["lsqp", "ifem"], default="lsqp", help="operator for --mode smoother")
@@ -87,6 +114,9 @@ def parse():
                    help="--mode discretisation: first level L (N = 2^(L+2))")
     p.add_argument("--compare-f64", action="store_true",
                    help="with --precision mixed: also time one plain FP64 solve and report the speedup")
+    p.add_argument("--no-mixed-c3", action="store_true",
+                   help="skip the mixed-precision vs FP64 solve on the N=128 shell reported beside the default line")
+    p.add_argument("--batch-rhs", type=int, default=32, help="--mode batch: right-hand sides of the batched solve")
     return p.parse_args()
 
 
@@ -175,9 +205,10 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 
 def traffic_record(kernel: str, workload: str):
-    """ncu DRAM bytes per launch of `kernel` on `workload`, if recorded for the
-    current kernel source (profiles/traffic.txt, JSON written from an ncu capture);
-    None when absent or when the source changed since the capture."""
+    """ncu DRAM bytes of one sweep (4 colour launches) of `kernel` on
+    `workload`, if recorded for the current kernel source (profiles/traffic.txt,
+    written by profiles/traffic_record.py from an ncu capture); None when
+    absent or when the source changed since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
@@ -187,7 +218,7 @@ def traffic_record(kernel: str, workload: str):
     src = open(os.path.join(ROOT, "paper_1608_06473_gb300", "csrc", rec["source"]), "rb").read()
     if hashlib.sha256(src).hexdigest()[:16] != rec["sha256_16"]:
         return None
-    return rec["dram_bytes_per_launch"]
+    return rec["dram_bytes_per_sweep"]
 
 
 def run_ours(args, rank, world, local):
@@ -218,6 +249,10 @@ def run_ours(args, rank, world, local):
     def updates(cycles):
         per_cycle = sum((nu1 + nu2 + 1) * free_per_level[l] for l in range(3, L + 1)) + free_per_level[L]
         return cycles * per_cycle + free_per_level[L]
+
+    # arithmetic peaks of this GPU, measured now (roofline denominators)
+    peaks = measure_peaks(hhg, stream)
+    hbm_gbs, hbm_note = hbm_peak()
 
     for _ in range(args.warmup):
         step(f, u)
@@ -285,7 +320,7 @@ def run_ours(args, rank, world, local):
     e2e = None
     if not args.no_e2e:
         fh = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_F)).pin_memory()
-        ke = max(1, min(args.steps, 2))
+        ke = max(1, min(args.steps, 5))
         uhs = [torch.zeros(n_total, dtype=torch.float64).pin_memory() for _ in range(ke)]   # u0 = 0 per step
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -298,34 +333,49 @@ def run_ours(args, rank, world, local):
         e2e = {"value": e_upd * world / te / 1e9, "unit": "GLUP/s", "h2d_bytes_per_step": 16 * n_total,
                "d2h_bytes_per_step": 8 * n_total, "steps": ke}
 
-    # one smoother launch updates every cell-interior node of the finest level once
+    # the dominant kernel: the finest level's cell-interior smoother, timed
+    # per sweep (4 colour launches, each updating one colour of every cell)
     N = 2 ** L
     n_cells = 20 * 4 ** tang * layers * 3
-    units_per_launch = n_cells * (N - 1) * (N - 2) * (N - 3) // 6
-    avg_launch_s = sm_ms * 1e-3 / max(sm_n, 1)
-    flops = LSQP_FLOPS[args.q] * units_per_launch
+    units_per_sweep = n_cells * (N - 1) * (N - 2) * (N - 3) // 6
+    sweep_s = sm_ms * 1e-3 / max(sm_n, 1)
+    common = {"sweeps": sm_n, "launches": 4 * sm_n, "avg_sweep_ms": sweep_s * 1e3,
+              "avg_launch_ms": sweep_s * 1e3 / 4, "units_per_sweep": units_per_sweep,
+              "units_per_launch": units_per_sweep / 4}
     if args.precision == "f64":
-        achieved = flops / avg_launch_s / 1e12
+        achieved = STENCIL_FLOPS * units_per_sweep / sweep_s / 1e12
+        traffic = traffic_record("lsqp_node_smooth_f64", args.workload)
         roofline = {"kernel": "lsqp_node_kernel<%d,SMOOTH> (finest level; one sweep = 4 colour launches)" % args.q,
-                    "bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_NOMINAL_TFLOPS,
-                    "traffic": traffic_record("lsqp_node_smooth_f64", args.workload),
-                    "peak_note": "FP64 nominal (recipe: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz)"}
+                    "bound": "alu", "achieved": achieved, "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
+                    "frac": achieved / peaks["fp64_tflops"],
+                    "traffic": traffic / 4 if traffic else None,
+                    "peak_note": "of measured: FP64 FMA throughput of this GPU measured in this run "
+                                 "(hhg_peak_rate, 2 flops per FMA)",
+                    "algorithmic": "29 FP64 flops per update (Eq. 5.1 with known weights: 14 FMA + 1 multiply by "
+                                   "the centre reciprocal; the kernel issues exactly these on the FP64 pipe)",
+                    "paper_flops": {"per_update": LSQP_FLOPS[args.q],
+                                    "tflops": LSQP_FLOPS[args.q] * units_per_sweep / sweep_s / 1e12,
+                                    "note": "Table 4.2 (29 + 15 q, weights included); the 15 q weight flops run in "
+                                            "exact integer arithmetic here, so this rate is not bounded by the FP64 "
+                                            "pipe"},
+                    "dram": {"algorithmic_gbs": 24 * units_per_sweep / sweep_s / 1e9,
+                             "measured_gbs": (traffic / (sweep_s / 4) / 1e9) if traffic else None,
+                             "peak_gbs": hbm_gbs, "peak_note": hbm_note,
+                             "frac": ((traffic / (sweep_s / 4) / 1e9) / hbm_gbs) if traffic else None}}
     else:
-        achieved = 12 * units_per_launch / avg_launch_s / 1e9
+        achieved = 12 * units_per_sweep / sweep_s / 1e9
         cfg = hhg.hhg_tuning(s.handle, L)[0]
         kname = ("lsqp_stage32_smooth<%d> (finest level, one launch per sweep, planes staged in shared memory; "
                  "tuned configuration %d)" % (args.q, cfg)) if cfg >= 0 else \
             ("lsqp_node32_%skernel<%d,SMOOTH> (finest level, tuned: one launch per colour)"
              % ("x2_" if cfg == -2 else "", args.q))
         roofline = {"kernel": kname,
-                    "bound": "hbm", "achieved": achieved, "peak": HBM_MEASURED_GBS, "unit": "GB/s",
-                    "frac": achieved / HBM_MEASURED_GBS,
-                    "traffic": traffic_record("lsqp_stage32_smooth", args.workload),
-                    "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)"}
-    roofline.update({"launches": sm_n, "avg_launch_ms": avg_launch_s * 1e3,
-                     "algorithmic_flops_per_launch": flops,
-                     "algorithmic_bytes_per_launch": (24 if args.precision == "f64" else 12) * units_per_launch})
+                    "bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s",
+                    "frac": achieved / hbm_gbs,
+                    "traffic": None,
+                    "peak_note": hbm_note,
+                    "algorithmic": "12 B per update (FP32 u read, f read, u written)"}
+    roofline.update(common)
     value = tot_updates * world / (ms * 1e-3) / 1e9
     out = {"metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -336,7 +386,7 @@ def run_ours(args, rank, world, local):
                       "cycle": "V(3,3)", "rtol": 1e-8, "unknowns": n_free, "nodes": n_total,
                       "l2": "inputs larger than L2 (each FP64 vector %.2f GB)" % (8 * n_total / 1e9),
                       "parallelism": "replicas" if world > 1 else "single"},
-           "clocks": clk, "gpu_launches": launches, "roofline": roofline,
+           "clocks": clk, "gpu_launches": launches, "roofline": roofline, "peaks": peaks,
            "e2e": e2e,
            "smoother_glups": {"lsqp": g_lsqp, "ifem": g_ifem, "lsqp_over_ifem": g_lsqp / g_ifem},
            "vcycle_s_to_1e-8": ms * 1e-3 / args.steps, "cycles": cyc_list, "final_relres": max(rels),
@@ -345,6 +395,74 @@ def run_ours(args, rank, world, local):
                                if args.precision == "mixed" else None),
            "speedup_over_f64_solve": (f64_solve["s"] / (ms * 1e-3 / args.steps)) if f64_solve else None}
     s.close()
+    del f, u
+    torch.cuda.empty_cache()
+    if world == 1 and args.precision == "f64" and not args.no_mixed_c3 and args.workload == "shell3840_N64":
+        mp = mixed_vs_f64("shell3840_N128", args.q, args.j)
+        out["mixed_precision"] = mp
+        out["speedup_over_f64_solve"] = mp["speedup_over_f64_solve"]
+        out["speedup_over_f64_solve_workload"] = mp["workload"]
+    return out
+
+
+def mixed_vs_f64(workload, q, j):
+    """The mixed-precision solve (FP32 surrogate evaluation, smoother and
+    transfers in V-cycles inside FP64 iterative refinement, FP64 fit and
+    coarsest solve) against the plain FP64 solve on the same shell and
+    right-hand side: V(3,3) to relative residual 1e-8 from u = 0, each timed
+    with CUDA events after a warm-up solve (fit excluded from the solve time,
+    reported apart), the difference of the two solutions, and the FP32
+    smoother's rate at this size."""
+    import torch
+
+    import paper_1608_06473_gb300 as hhg
+    import synthetic
+    tang, layers, L, desc = WORKLOADS[workload]
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    s = hhg.Shell(0.55, 1.0, tang, layers, L, stream=stream)
+    n_total, n_free = s.num_nodes()
+    f = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_F)).cuda()
+    out = {"workload": workload, "shell": desc, "nodes": n_total, "unknowns": n_free, "cycle": "V(3,3)",
+           "rtol": 1e-8}
+    sol = {}
+    for name, dtype in (("mixed", hhg.HHG_F32), ("f64", hhg.HHG_F64)):
+        uu = torch.zeros_like(f)
+        a, b = ev(), ev()
+        a.record(stream)
+        s.fit(q, j, stream=stream)
+        b.record(stream)
+        s.vcycle(f, uu, 3, 3, max_cycles=60, rtol=1e-8, dtype=dtype, stream=stream)   # warm-up
+        torch.cuda.synchronize()
+        fit_s = a.elapsed_time(b) * 1e-3
+        uu.zero_()
+        hhg.hhg_timing(s.handle, True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        rel, cyc, _ = s.vcycle(f, uu, 3, 3, max_cycles=60, rtol=1e-8, dtype=dtype, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        sm_ms, sm_n = hhg.hhg_timing_read(s.handle, hhg.HHG_T_CELL_SMOOTH)
+        hhg.hhg_timing(s.handle, False)
+        out[name] = {"solve_s": a.elapsed_time(b) * 1e-3, "fit_s": fit_s, "cycles": cyc, "relres": float(rel[0]),
+                     "cell_sweep_ms": sm_ms / max(sm_n, 1)}
+        sol[name] = uu
+    out["speedup_over_f64_solve"] = out["f64"]["solve_s"] / out["mixed"]["solve_s"]
+    out["mixed_vs_f64_rel_l2"] = float(torch.linalg.vector_norm(sol["mixed"] - sol["f64"]) /
+                                       torch.linalg.vector_norm(sol["f64"]))
+    N = 2 ** L
+    units = 20 * 4 ** tang * layers * 3 * (N - 1) * (N - 2) * (N - 3) // 6
+    hbm_gbs, hbm_note = hbm_peak()
+    sweep = out["mixed"]["cell_sweep_ms"] * 1e-3
+    cfg = hhg.hhg_tuning(s.handle, L)[0]
+    out["fp32_smoother"] = {"tuned_cfg": cfg, "cell_sweep_ms": sweep * 1e3, "glups": units / sweep / 1e9,
+                            "algorithmic_gbs": 12 * units / sweep / 1e9, "hbm_frac": 12 * units / sweep / 1e9 / hbm_gbs,
+                            "peak_note": hbm_note}
+    out["f64_smoother"] = {"cell_sweep_ms": out["f64"]["cell_sweep_ms"],
+                           "glups": units / (out["f64"]["cell_sweep_ms"] * 1e-3) / 1e9}
+    s.close()
+    del f, sol
+    torch.cuda.empty_cache()
     return out
 
 
@@ -378,12 +496,61 @@ def oracle_sample(workload, n_cells, sweeps, seed=7):
     return upd, sec
 
 
+def _oracle_worker(job):
+    workload, sweeps, seed = job
+    return oracle_sample(workload, 1, sweeps, seed=seed)
+
+
+def host_info():
+    model = None
+    try:
+        for line in subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+def oracle_c1_vcycle():
+    """Seconds of one V(3,3) cycle of the full oracle (global CSR operators,
+    sparse direct coarse solve) on the 60-cell shell at N = 16, LSQP q = 2,
+    from u = 0 with the seed-0 right-hand side (hierarchy assembly excluded)."""
+    import synthetic
+    from oracle import mesh as M
+    from oracle import mg
+    H = mg.build_hierarchy(M.make_shell(), 16, "lsqp", 2, 2)
+    n = H.levels[-1].n_total
+    f = synthetic.uniform(n, synthetic.SEED_F)
+    t0 = time.perf_counter()
+    H.vcycle(len(H.ops) - 1, np.zeros(n), f)
+    return time.perf_counter() - t0
+
+
 def cpu_baseline(workload, n_cells=6, sweeps=60):
+    """The oracle timed on this host: one core on a bounded sample of the
+    workload (LSQP multicolour GS sweeps over the interior rows of seeded
+    macro cells), the same on every core (one process per core, spawned, each
+    sweeping its own seeded cell), and one full-oracle V-cycle at 60 cells,
+    N = 16."""
+    import multiprocessing as mp
     upd, sec = oracle_sample(workload, n_cells, sweeps)
+    host = host_info()
+    cores = host["nproc"] or 1
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(workload, sweeps, 50 + k) for k in range(cores)])
+    all_upd = sum(r[0] for r in res)
+    all_sec = max(r[1] for r in res)
     return {"value": upd / sec / 1e9, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
             "sample": f"oracle LSQP multicolour GS, {sweeps} sweeps over the interior rows of {n_cells} seeded "
                       f"macro cells of {workload} (FP64 NumPy, one core; assembly and fit excluded)",
-            "seconds": sec}
+            "seconds": sec, "host": host,
+            "all_cores": {"value": all_upd / all_sec / 1e9, "unit": "GLUP/s", "cores": cores,
+                          "sample": f"{cores} spawned processes, each {sweeps} sweeps over one seeded macro cell "
+                                    f"of {workload}; total updates / slowest process's sweep time"},
+            "c1_vcycle_s": oracle_c1_vcycle(),
+            "c1_vcycle_note": "one V(3,3) cycle of the full oracle, 60 cells, N = 16, LSQP q = 2 (one core)"}
 
 
 def run_reference(args, rank, world):
@@ -404,7 +571,8 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "shell": desc, "op": "lsqp", "q": 2, "j": 2},
             "cpu_baseline": {"value": v, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
-                             "sample": f"per step: {sweeps} oracle LSQP GS sweeps over {n_cells} seeded macro cells"},
+                             "sample": f"per step: {sweeps} oracle LSQP GS sweeps over {n_cells} seeded macro cells",
+                             "host": host_info()},
             "e2e": {"value": v, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -412,16 +580,19 @@ SERVE_RADII = [0.35 + 0.05 * k for k in range(8)]   # inner radii of the request
 SERVE_LEVELS = [4, 5, 6, 7]                          # N = 16 .. 128 on the 60-macro shell
 
 
-def serve_run(n_requests, rate_hz=200.0, seed=2024, max_inflight=4, warm=True, max_batch_rhs=16):
+def serve_run(n_requests, rate_hz=200.0, seed=2024, max_inflight=4, warm_fraction=0.5, max_batch_rhs=16,
+              hbm_budget_gb=32.0):
     """Poisson stream of shell solves through the library's request loop
     (hhg_server_*): levels 4-7 and inner radius (from an 8-point grid in
     [0.35, 0.7]) drawn uniformly, 1-8 right-hand sides uniform[-1, 1] each,
-    mixed precision to relative residual 1e-8.  With warm=True every
-    (radius, level) hierarchy is built once before the timed stream, so the
-    stream measures the resident-hierarchy steady state.  max_batch_rhs > 1
-    turns on continuous batching (queued requests of one key merged into one
-    batched solve).  Returns latency percentiles and throughput from the
-    library's own per-request stamps."""
+    mixed precision to relative residual 1e-8, under an HBM budget.  A
+    `warm_fraction` of the 32 (radius, level) hierarchies is built before the
+    timed stream; the others are built inside it, evicting idle hierarchies
+    when the budget requires.  max_batch_rhs > 1 turns on continuous batching
+    (queued requests of one key merged into one batched solve).  Returns, from
+    the library's own per-request stamps, end-to-end latency, queue wait
+    (submit to start) and service time (start to end) percentiles,
+    throughput, and the builds and evictions during the stream."""
     import paper_1608_06473_gb300 as hhg
     import synthetic
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -436,12 +607,15 @@ def serve_run(n_requests, rate_hz=200.0, seed=2024, max_inflight=4, warm=True, m
             pool[L] = np.stack([synthetic.uniform(n, 900 + b) for b in range(8)])
         return pool[L][:nr]
 
-    srv = hhg.Server(max_inflight=max_inflight, dtype=hhg.HHG_F32, rtol=1e-8, max_batch_rhs=max_batch_rhs)
+    keys = [(ri, L) for ri in SERVE_RADII for L in SERVE_LEVELS]
+    warm_keys = keys[::int(round(1 / warm_fraction))] if warm_fraction > 0 else []
+    srv = hhg.Server(hbm_budget_bytes=int(hbm_budget_gb * 1e9), max_inflight=max_inflight, dtype=hhg.HHG_F32,
+                     rtol=1e-8, max_batch_rhs=max_batch_rhs)
     try:
-        if warm:
-            ts = [srv.submit(rhs(ri, L, 1), r_inner=ri, L=L) for ri in SERVE_RADII for L in SERVE_LEVELS]
-            for t in ts:
-                srv.wait(t)
+        ts = [srv.submit(rhs(ri, L, 1), r_inner=ri, L=L) for ri, L in warm_keys]
+        for t in ts:
+            srv.wait(t)
+        st0 = srv.stats()
         for ri, L, nr in reqs:
             rhs(ri, L, nr)
         t0 = time.perf_counter()
@@ -461,21 +635,33 @@ def serve_run(n_requests, rate_hz=200.0, seed=2024, max_inflight=4, warm=True, m
     finally:
         srv.close()
     lat = np.array([i["t_end"] - i["t_submit"] for i in infos])
+    wait = np.array([i["t_start"] - i["t_submit"] for i in infos])
+    svc = np.array([i["t_end"] - i["t_start"] for i in infos])
     span = max(i["t_end"] for i in infos) - min(i["t_submit"] for i in infos)
     n_rhs = sum(nr for _, _, nr in reqs)
+    pct = lambda x, q: float(np.percentile(x, q))
     return {"requests": n_requests, "arrival_rate_hz": rate_hz, "max_inflight": max_inflight,
-            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-            "mean_latency_s": float(lat.mean()), "throughput_req_s": n_requests / span,
-            "throughput_rhs_s": n_rhs / span, "worst_relres": worst,
-            "reused": int(sum(i["reused"] for i in infos)), "resident_hierarchies": stats["resident"],
+            "p50_latency_s": pct(lat, 50), "p99_latency_s": pct(lat, 99), "mean_latency_s": float(lat.mean()),
+            "p50_queue_wait_s": pct(wait, 50), "p99_queue_wait_s": pct(wait, 99),
+            "p50_service_s": pct(svc, 50), "p99_service_s": pct(svc, 99),
+            "throughput_req_s": n_requests / span, "throughput_rhs_s": n_rhs / span,
+            "offered_load_note": "arrivals (%g req/s) exceed the measured throughput, so end-to-end latency is "
+                                 "mostly queue wait; service time is the solve itself (with a build when the "
+                                 "hierarchy was not resident)" % rate_hz,
+            "worst_relres": worst,
+            "reused": int(sum(i["reused"] for i in infos)),
+            "built_in_stream": stats["built"] - st0["built"], "evicted_in_stream": stats["evicted"] - st0["evicted"],
+            "prebuilt_keys": len(warm_keys), "keys": len(keys), "hbm_budget_gb": hbm_budget_gb,
+            "resident_hierarchies": stats["resident"],
             "max_batch_rhs": max_batch_rhs,
             "merged_requests": int(sum(i["batch_rhs"] > nr for i, (_, _, nr) in zip(infos, reqs))),
             "mean_batch_rhs": float(np.mean([i["batch_rhs"] for i in infos])),
             "resident_gb": stats["bytes"] / 1e9,
             "workload": "Poisson arrivals (mean %g req/s) of shell solves on the 60-macro icosahedral shell, "
                         "levels 4-7 (N=16..128) and r_inner in {0.35,0.40,...,0.70} drawn uniformly, 1-8 "
-                        "right-hand sides uniform[-1,1]; mixed precision, V(3,3) to 1e-8; hierarchies "
-                        "resident (built before the stream)" % rate_hz}
+                        "right-hand sides uniform[-1,1]; mixed precision, V(3,3) to 1e-8; HBM budget %g GB; "
+                        "%d of %d hierarchies built before the stream, the rest inside it"
+                        % (rate_hz, hbm_budget_gb, len(warm_keys), len(keys))}
 
 
 def run_variants(args):
@@ -601,6 +787,104 @@ def run_discretisation(args):
             "load_vector": "vertex quadrature (hhg_load_vector)", "rows": rows}
 
 
+BATCH_RADII = [0.35 + 0.05 * k for k in range(8)]   # inner radii of the 8-shell group
+
+
+def run_batch(args):
+    """The batched configuration: (A) --batch-rhs Gaussian right-hand sides
+    (sigma = 1, seeds 100 + b) on the 3840-macro shell at N = 32, solved
+    together (every node's weights formed once for all of them) by
+    mixed-precision V(3,3) cycles (FP32 smoothing, transfers and surrogate,
+    FP64 refinement and coarsest solve) replayed from a CUDA graph, to
+    relative residual 1e-8 each; against the same solve of right-hand side 0
+    alone.  (B) 8 shells of inner radius 0.35 .. 0.70 (3840 macros each) as
+    one hierarchy per level, levels 4, 5, 6 (every kernel launch spans the 8
+    shells of a level), one Gaussian right-hand side per shell.  Times are
+    CUDA events around the solve after a warm-up solve; the fit is timed
+    apart."""
+    import torch
+
+    import paper_1608_06473_gb300 as hhg
+    import synthetic
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    tang, layers = 2, 4
+
+    def solve(s, F, nrhs, free_per_level, L):
+        U = torch.zeros_like(F)
+        s.vcycle(F, U, 3, 3, max_cycles=60, rtol=1e-8, dtype=hhg.HHG_F32, nrhs=nrhs, stream=stream)   # warm-up
+        U.zero_()
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        rel, cyc, _ = s.vcycle(F, U, 3, 3, max_cycles=60, rtol=1e-8, dtype=hhg.HHG_F32, nrhs=nrhs, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        sec = a.elapsed_time(b) * 1e-3
+        per_cycle = sum(7 * free_per_level[l] for l in range(3, L + 1)) + free_per_level[L]
+        upd = nrhs * (cyc * per_cycle + free_per_level[L])
+        return {"s": sec, "cycles": cyc, "max_relres": float(np.max(rel)), "glups": upd / sec / 1e9,
+                "s_per_rhs": sec / nrhs}
+
+    out = {"mode": "batch"}
+    L = 5
+    s = hhg.Shell(0.55, 1.0, tang, layers, L, stream=stream)
+    n_total, n_free = s.num_nodes()
+    fpl = {l: s.num_nodes(l)[1] for l in range(2, L + 1)}
+    a, b = ev(), ev()
+    a.record(stream)
+    s.fit(2, 2, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    nb = args.batch_rhs
+    F = torch.from_numpy(synthetic.batch(n_total, nb, "gaussian")).cuda()
+    one = solve(s, F[0].clone(), 1, fpl, L)
+    many = solve(s, F, nb, fpl, L)
+    out["A"] = {"shell": "3840 macro cells, N=32, r in [0.55, 1]", "nodes": n_total, "unknowns": n_free,
+                "nrhs": nb, "rhs": "Gaussian sigma=1, seeds 100+b", "fit_s": a.elapsed_time(b) * 1e-3,
+                "single": one, "batched": many,
+                "per_rhs_speedup": one["s"] / many["s_per_rhs"],
+                "graphs": "V-cycles 2.. replayed from one CUDA graph"}
+    s.close()
+    del F
+    torch.cuda.empty_cache()
+    rows = []
+    for Lg in (4, 5, 6):
+        radii = [(ri, 1.0) for ri in BATCH_RADII]
+        g = hhg.Shell.group(radii, tang, layers, Lg, stream=stream)
+        nt, nf = g.num_nodes()
+        fpl = {l: g.num_nodes(l)[1] for l in range(2, Lg + 1)}
+        a, b = ev(), ev()
+        a.record(stream)
+        g.fit(2, 2, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        Fg = torch.from_numpy(synthetic.gaussian(nt, synthetic.SEED_BATCH0)).cuda()
+        r = solve(g, Fg, 1, fpl, Lg)
+        r.update({"L": Lg, "N": 2 ** Lg, "shells": len(radii), "macro_cells": 8 * 3840, "nodes": nt,
+                  "unknowns": nf, "fit_s": a.elapsed_time(b) * 1e-3})
+        rows.append(r)
+        g.close()
+        del Fg
+        torch.cuda.empty_cache()
+    out["B"] = {"shells": "8 shells, r_inner = 0.35, 0.40, ..., 0.70, r_outer = 1, 3840 macro cells each, one "
+                          "hierarchy per level (every launch spans the 8 shells)", "levels": rows,
+                "total_s": sum(r["s"] for r in rows)}
+    return out
+
+
+def run_peaks(args):
+    import torch
+
+    import paper_1608_06473_gb300 as hhg
+    torch.cuda.init()
+    out = measure_peaks(hhg)
+    out["int32_imad_per_s"] = hhg.hhg_peak_rate(hhg.PEAK_INT32_IMAD)[0]
+    out["hbm"] = dict(zip(("gbs", "note"), hbm_peak()))
+    out["mode"] = "peaks"
+    return out
+
+
 def run_smoother(args):
     """Finest-level smoother only: setup, fit, `warmup` sweeps, then `steps`
     sweeps timed with CUDA events on the launching stream."""
@@ -651,6 +935,12 @@ def main():
         return
     if args.mode == "discretisation":
         print(json.dumps(run_discretisation(args)))
+        return
+    if args.mode == "batch":
+        print(json.dumps(run_batch(args)))
+        return
+    if args.mode == "peaks":
+        print(json.dumps(run_peaks(args)))
         return
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))

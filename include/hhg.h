@@ -313,8 +313,10 @@ hhg_status hhg_server_submit(hhg_server* srv, const hhg_problem* p, const double
 hhg_status hhg_server_wait(hhg_server* srv, int64_t ticket, double* u_host, double* relres,
                            hhg_request_info* info);
 
-/* Resident hierarchies and their bytes (diagnostics). */
-hhg_status hhg_server_stats(hhg_server* srv, int* n_resident, size_t* bytes_resident, int64_t* n_built);
+/* Resident hierarchies and their bytes, and the hierarchies built and
+ * evicted since hhg_server_create (diagnostics; every pointer nullable). */
+hhg_status hhg_server_stats(hhg_server* srv, int* n_resident, size_t* bytes_resident, int64_t* n_built,
+                            int64_t* n_evicted);
 
 /* Waits for every queued request, then frees all hierarchies. */
 hhg_status hhg_server_destroy(hhg_server* srv);
@@ -379,17 +381,46 @@ hhg_status hhg_timing_read(hhg_shell* shell, int which, double* total_ms, int64_
  * thread-per-node kernel, -2 for the same with two nodes per thread in
  * flight, 0..3 for the shared-memory staged one-launch kernel with
  * (wavefront skew, threads per CTA) = (1, 256), (1, 1024), (2, 128),
- * (2, 512); -9 if not tuned.  ms (nullable, 6 entries) receives each
- * candidate's best time for one cell sweep, candidate cfg at ms[cfg + 2]
- * (-1 = not run).  The FP32 apply and residual use the two-nodes variant
- * when the smoother does. */
+ * (2, 512), 4..5 for the plane-wavefront one-launch kernel (u in place
+ * through the caches) with 256 and 512 threads per CTA; -9 if not tuned.
+ * ms (nullable, 8 entries) receives each candidate's best time for one cell
+ * sweep, candidate cfg at ms[cfg + 2] (-1 = not run).  The FP32 apply and
+ * residual use the two-nodes variant when the smoother does.  Batched calls
+ * (nrhs > 1) smooth with the per-colour kernel that forms every node's
+ * weights once for all right-hand sides. */
 hhg_status hhg_tuning(const hhg_shell* shell, int L, int* cfg, double* ms);
 
-/* Pins the FP32 surrogate smoother of level L to configuration cfg (-2, -1
- * or a staged configuration 0..3 as above) until the next fit; a staged
- * configuration that does not fit the level falls back to the per-colour
- * kernel at launch.  HHG_EINVAL for an unknown cfg. */
+/* Pins the FP32 surrogate smoother of level L to configuration cfg (-2, -1,
+ * a staged configuration 0..3 or a wavefront configuration 4..5 as above)
+ * until the next fit; a one-launch configuration that does not fit the
+ * level falls back to the per-colour kernel at launch.  HHG_EINVAL for an
+ * unknown cfg. */
 hhg_status hhg_set_tuning(hhg_shell* shell, int L, int cfg);
+
+/* Throughput of one arithmetic pipe on the current device (the paper has
+ * no counterpart: these are the roofline denominators of the FP64 and FP32
+ * stencil kernels).  kind 0: FP64 fused multiply-add, 1: FP32 fused
+ * multiply-add, 2: INT32 multiply-add.  A kernel of 8 independent
+ * multiply-add chains per thread, 8 CTAs of 256 threads per SM, runs for
+ * about 150 ms (calibrated), best of three; *ops_per_s receives the
+ * multiply-adds per second (one FMA = 2 flops), *ms (nullable) the time of
+ * the best run.  Waits for the stream; allocates a small output buffer on
+ * it (stream-ordered). */
+hhg_status hhg_peak_rate(int kind, double* ops_per_s, double* ms, void* stream);
+
+/* The hand-written arithmetic helpers of the surrogate kernels applied
+ * elementwise to n device values (the paper has no counterpart; tests
+ * compare them with the IEEE operations):
+ *   which 0: out[t] = a[t] / b[t], FP32, reciprocal estimate + one
+ *            Newton-Raphson step (the staged FP32 smoother's divide);
+ *   which 1: out[t] = 2^E / W with W = ((const int64_t*) a)[t] != 0 and
+ *            E = ((const int*) b)[t]: the integer-pipe reciprocal of the
+ *            FP64 surrogate's centre weight (FP32 estimate, two fixed-point
+ *            Newton-Raphson steps);
+ *   which 2: out[t] = W 2^-E (W, E as for 1), integer-pipe conversion with
+ *            the scale undone, truncated toward zero.
+ * Device pointers; does not wait. */
+hhg_status hhg_check_arith(int which, const void* a, const void* b, void* out, int64_t n, void* stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* hhg_last_error(void);

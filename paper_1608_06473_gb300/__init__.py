@@ -96,13 +96,15 @@ _SIGS = {
     "hhg_server_submit": [_P, ctypes.POINTER(hhg_problem), _P, _I, ctypes.POINTER(ctypes.c_int64)],
     "hhg_server_wait": [_P, ctypes.c_int64, _P, _P, ctypes.POINTER(hhg_request_info)],
     "hhg_server_stats": [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t),
-                         ctypes.POINTER(ctypes.c_int64)],
+                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "hhg_server_destroy": [_P],
     "hhg_timing": [_P, _I],
     "hhg_tuning": [_P, _I, ctypes.POINTER(ctypes.c_int), _P],
     "hhg_set_tuning": [_P, _I, _I],
     "hhg_set_graphs": [_P, _I],
     "hhg_timing_read": [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
+    "hhg_peak_rate": [_I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _P],
+    "hhg_check_arith": [_I, _P, _P, _P, ctypes.c_int64, _P],
 }
 
 
@@ -151,10 +153,29 @@ def hhg_timing_read(shell: int, which: int):
     return ms.value, n.value
 
 
+PEAK_FP64_FMA, PEAK_FP32_FMA, PEAK_INT32_IMAD = 0, 1, 2
+
+
+def hhg_peak_rate(kind: int, stream=None):
+    """(multiply-adds per second, ms of the best timed run) of one arithmetic
+    pipe on the current device (kind: PEAK_FP64_FMA, PEAK_FP32_FMA,
+    PEAK_INT32_IMAD)."""
+    r, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().hhg_peak_rate(kind, ctypes.byref(r), ctypes.byref(ms), _stream(stream)))
+    return r.value, ms.value
+
+
+def hhg_check_arith(which: int, a, b, out, n: int, stream=None):
+    """The kernels' hand-written arithmetic helpers applied elementwise
+    (which 0: FP32 divide, 1: 2^E / W on the integer pipe, 2: W 2^-E on the
+    integer pipe; W int64, E int32); device tensors."""
+    _check(lib().hhg_check_arith(which, _ptr(a), _ptr(b), _ptr(out), n, _stream(stream)))
+
+
 def hhg_tuning(shell: int, L: int):
     """(chosen FP32 smoother configuration, per-candidate ms) of level L."""
     cfg = ctypes.c_int()
-    ms = np.zeros(6)
+    ms = np.zeros(8)
     _check(lib().hhg_tuning(shell, L, ctypes.byref(cfg), ms.ctypes.data))
     return cfg.value, ms
 
@@ -190,6 +211,37 @@ def _ptr(x) -> int:
             raise ValueError("tensors must be contiguous")
         return x.data_ptr()
     raise TypeError(f"unsupported vector type {type(x)}")
+
+
+def _vec(x, n, what, f32=False, device_only=False) -> int:
+    """_ptr(x) after checking that x (a NumPy array or a torch tensor) holds
+    at least n values of the type the call reads: float64, or float32 when
+    f32 (tensors only; host vectors are always float64).  The C side cannot
+    check lengths, so a short or mistyped vector would be read or written
+    out of bounds.  Raw integer addresses are passed through unchecked."""
+    if x is None or isinstance(x, int):
+        return _ptr(x)
+    if isinstance(x, np.ndarray):
+        if device_only:
+            raise ValueError(f"{what}: this call takes device vectors only")
+        if x.size < n:
+            raise ValueError(f"{what}: {x.size} values, the call needs {n}")
+        return _ptr(x)
+    if hasattr(x, "data_ptr"):
+        import torch
+        want = torch.float32 if f32 else torch.float64
+        if x.dtype != want:
+            raise ValueError(f"{what}: dtype {x.dtype}, the call needs {want}")
+        if device_only and not x.is_cuda:
+            raise ValueError(f"{what}: this call takes device vectors only")
+        if x.numel() < n:
+            raise ValueError(f"{what}: {x.numel()} values, the call needs {n}")
+        return _ptr(x)
+    return _ptr(x)
+
+
+def _n(shell: int, L: int) -> int:
+    return hhg_num_nodes(shell, L)[0]
 
 
 def _stream(stream) -> int:
@@ -266,31 +318,41 @@ def hhg_fit_cons(shell: int, q: int = 2, j: int = 2, stream=None):
 
 
 def hhg_load_vector(shell: int, L: int, f, b, stream=None):
-    _check(lib().hhg_load_vector(shell, L, _ptr(f), _ptr(b), _stream(stream)))
+    n = _n(shell, L)
+    _check(lib().hhg_load_vector(shell, L, _vec(f, n, "f"), _vec(b, n, "b"), _stream(stream)))
 
 
 def hhg_apply(shell: int, L: int, op: int, dtype: int, u, y, nrhs: int = 1, stream=None):
-    _check(lib().hhg_apply(shell, L, op, dtype, _ptr(u), _ptr(y), nrhs, _stream(stream)))
+    n, f32 = _n(shell, L) * nrhs, dtype == HHG_F32
+    _check(lib().hhg_apply(shell, L, op, dtype, _vec(u, n, "u", f32), _vec(y, n, "y", f32), nrhs, _stream(stream)))
 
 
 def hhg_residual(shell: int, L: int, op: int, dtype: int, u, f, r, nrhs: int = 1, want_norms: bool = True,
                  stream=None):
     norms = np.zeros(nrhs) if want_norms else None
-    _check(lib().hhg_residual(shell, L, op, dtype, _ptr(u), _ptr(f), _ptr(r), nrhs,
+    n, f32 = _n(shell, L) * nrhs, dtype == HHG_F32
+    _check(lib().hhg_residual(shell, L, op, dtype, _vec(u, n, "u", f32), _vec(f, n, "f", f32), _vec(r, n, "r", f32),
+                              nrhs,
                               norms.ctypes.data if want_norms else None, _stream(stream)))
     return norms
 
 
 def hhg_smooth(shell: int, L: int, op: int, dtype: int, f, u, sweeps: int = 1, nrhs: int = 1, stream=None):
-    _check(lib().hhg_smooth(shell, L, op, dtype, _ptr(f), _ptr(u), sweeps, nrhs, _stream(stream)))
+    n, f32 = _n(shell, L) * nrhs, dtype == HHG_F32
+    _check(lib().hhg_smooth(shell, L, op, dtype, _vec(f, n, "f", f32), _vec(u, n, "u", f32), sweeps, nrhs,
+                            _stream(stream)))
 
 
 def hhg_vcycle(shell: int, op: int, dtype: int, f, u, nu1: int = 3, nu2: int = 3, max_cycles: int = 50,
-               rtol: float = 1e-8, nrhs: int = 1, stream=None, raise_on_noconv: bool = True):
-    """Returns (relres per right-hand side, cycles run, status)."""
+               rtol: float = 1e-8, nrhs: int = 1, stream=None, raise_on_noconv: bool = True, L=None):
+    """Returns (relres per right-hand side, cycles run, status).  f and u are
+    FP64 in both precisions; with L (the finest level) their lengths are
+    checked."""
     rel = np.zeros(nrhs)
     cyc = ctypes.c_int()
-    st = lib().hhg_vcycle(shell, op, dtype, _ptr(f), _ptr(u), nu1, nu2, max_cycles, rtol, nrhs, rel.ctypes.data,
+    n = _n(shell, L) * nrhs if L is not None else 0
+    st = lib().hhg_vcycle(shell, op, dtype, _vec(f, n, "f"), _vec(u, n, "u"), nu1, nu2, max_cycles, rtol, nrhs,
+                          rel.ctypes.data,
                           ctypes.byref(cyc), _stream(stream))
     if st != HHG_OK and (st != HHG_ENOCONV or raise_on_noconv):
         raise HHGError(st, hhg_last_error())
@@ -302,8 +364,14 @@ HHG_NOALLOC_SCRATCH = 16384
 
 def hhg_residual_noalloc(shell: int, L: int, op: int, u, f, r, norm2_dev, stream=None):
     """r = f - L u and ||r||^2 into the device double norm2_dev, allocating
-    nothing (device pointers only; see include/hhg.h)."""
-    _check(lib().hhg_residual_noalloc(shell, L, op, _ptr(u), _ptr(f), _ptr(r), _ptr(norm2_dev), _stream(stream)))
+    nothing (device pointers only; see include/hhg.h).  Tensors are checked
+    for type, device and length here (u, f, r: CUDA float64 with at least
+    n_total values; norm2_dev: CUDA float64 with at least one), because the
+    C side cannot see lengths; raw integer addresses are passed unchecked."""
+    n = _n(shell, L)
+    _check(lib().hhg_residual_noalloc(shell, L, op, _vec(u, n, "u", device_only=True),
+                                      _vec(f, n, "f", device_only=True), _vec(r, n, "r", device_only=True),
+                                      _vec(norm2_dev, 1, "norm2_dev", device_only=True), _stream(stream)))
 
 
 class Shell:
@@ -381,7 +449,8 @@ class Shell:
 
     def vcycle(self, f, u, nu1=3, nu2=3, max_cycles=50, rtol=1e-8, op=HHG_OP_LSQP, dtype=HHG_F64, nrhs=1,
                stream=None, raise_on_noconv=True):
-        return hhg_vcycle(self.handle, op, dtype, f, u, nu1, nu2, max_cycles, rtol, nrhs, stream, raise_on_noconv)
+        return hhg_vcycle(self.handle, op, dtype, f, u, nu1, nu2, max_cycles, rtol, nrhs, stream, raise_on_noconv,
+                          L=self.L)
 
 
 def hhg_problem_nodes(r_inner, r_outer, tang_refine, radial_layers, L):
@@ -427,9 +496,10 @@ class Server:
                         "batch_rhs": info.batch_rhs}
 
     def stats(self):
-        n, b, built = ctypes.c_int(), ctypes.c_size_t(), ctypes.c_int64()
-        _check(lib().hhg_server_stats(self.handle, ctypes.byref(n), ctypes.byref(b), ctypes.byref(built)))
-        return {"resident": n.value, "bytes": b.value, "built": built.value}
+        n, b, built, ev = ctypes.c_int(), ctypes.c_size_t(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().hhg_server_stats(self.handle, ctypes.byref(n), ctypes.byref(b), ctypes.byref(built),
+                                      ctypes.byref(ev)))
+        return {"resident": n.value, "bytes": b.value, "built": built.value, "evicted": ev.value}
 
     def close(self):
         if self.handle:

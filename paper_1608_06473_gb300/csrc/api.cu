@@ -409,7 +409,7 @@ LevelView<double> view<double>(hhg_shell* s, int n) {
   v.plane_x = L.d_plane_x; v.plane_nb = L.d_plane_nb; v.n_plane = L.n_plane;
   v.bnd_ijk = L.d_bnd_ijk; v.bnd_slot = L.d_bnd_slot; v.halo_src = L.d_halo_src; v.ghost = L.d_ghost64;
   v.coef = L.d_coef; v.q = (L.d_coef && L.N >= 8) ? s->q : 0;
-  v.line64 = L.d_line64; v.cell_e = L.d_cell_e; v.n_lines = (int)n_cell_lines(L.N);
+  v.plane64 = L.d_plane64; v.cell_e = L.d_cell_e;
   v.colour_nodes = L.d_colour_nodes;
   v.all_nodes = L.d_all_nodes;
   for (int cc = 0; cc < 5; ++cc) v.colour_off[cc] = L.colour_off[cc];
@@ -467,9 +467,9 @@ static void tune_smooth32(hhg_shell* s, cudaStream_t st) {
     v.nrhs = 1;
     float best_ms = 0.0f;
     int best = -1;
-    for (int cfg = -2; cfg < STAGE32_CONFIGS; ++cfg) {
+    for (int cfg = -2; cfg < SMOOTH32_CONFIGS; ++cfg) {
       L.tune32_ms[cfg + 2] = -1.0;
-      if (cfg >= 0 && !stage32_supported(v, L.d_u32, cfg)) continue;
+      if (cfg >= 0 && !smooth32_supported(v, L.d_u32, cfg)) continue;
       v.smooth_cfg = cfg;
       launch_cell(v, HHG_OP_LSQP, SMOOTH, L.d_u32, L.d_u32, (const float*)L.d_f32, nullptr, st);
       float ms = 1e30f;
@@ -865,14 +865,14 @@ static void fit(hhg_shell* s, int q, int j, cudaStream_t st, bool ipoly = false,
     double* d_P = upload(A, P, st);
     double* d_sc = upload(A, sc, st);
     const size_t ncoef = (size_t)L.lay.nC * 15 * mq;
-    const size_t nline = (size_t)L.lay.nC * n_cell_lines(N) * line_rec(q);
+    const size_t nplane64 = (size_t)plane64_len(L.lay.nC, N, q);
     if (s->q != q || !L.d_coef) {  // (re)allocate only when the degree changes
-      for (void* p : {(void*)L.d_coef, (void*)L.d_coef32, (void*)L.d_line64, (void*)L.d_cell_e, (void*)L.d_plane32})
+      for (void* p : {(void*)L.d_coef, (void*)L.d_coef32, (void*)L.d_plane64, (void*)L.d_cell_e, (void*)L.d_plane32})
         A.release(p);
       L.d_plane32 = A.alloc_n<float>((size_t)plane_table_len((int)L.lay.nC, N, q));
       L.d_coef = A.alloc_n<double>(ncoef);
       L.d_coef32 = A.alloc_n<float>(ncoef);
-      L.d_line64 = A.alloc_n<long long>(nline);
+      L.d_plane64 = A.alloc_n<long long>(nplane64);
       L.d_cell_e = A.alloc_n<int>((size_t)L.lay.nC);
     }
     // sample in chunks of cells so the sample buffer stays below ~1 GB
@@ -889,7 +889,7 @@ static void fit(hhg_shell* s, int q, int j, cudaStream_t st, bool ipoly = false,
       launch_fit_coef(nc, mq, np, d_P, d_sc, d_b, L.d_coef + (int64_t)c0 * 15 * mq, L.d_coef32 + (int64_t)c0 * 15 * mq,
                       st);
     }
-    launch_line_table(v, q, L.d_coef, L.d_cell_e, L.d_line64, st);
+    launch_plane64_table(v, q, L.d_coef, L.d_cell_e, L.d_plane64, st);
     launch_plane_table(v, q, L.d_coef, L.d_plane32, st);
     HHG_CUDA(cudaStreamSynchronize(st));
     A.release(d_b);
@@ -1155,7 +1155,7 @@ hhg_status hhg_tuning(const hhg_shell* s, int L, int* cfg, double* ms) {
     const Level& Lv = s->levels[n];
     if (cfg) *cfg = Lv.tune32;
     if (ms)
-      for (int t = 0; t < 2 + STAGE32_CONFIGS; ++t) ms[t] = Lv.tune32 == TUNE_NONE ? -1.0 : Lv.tune32_ms[t];
+      for (int t = 0; t < 2 + SMOOTH32_CONFIGS; ++t) ms[t] = Lv.tune32 == TUNE_NONE ? -1.0 : Lv.tune32_ms[t];
   });
 }
 
@@ -1169,7 +1169,7 @@ hhg_status hhg_set_graphs(hhg_shell* s, int enable) {
 hhg_status hhg_set_tuning(hhg_shell* s, int L, int cfg) {
   return guarded([&] {
     const int n = level_index(s, L);
-    HHG_CHECK(cfg >= -2 && cfg < STAGE32_CONFIGS, HHG_EINVAL, "unknown smoother configuration");
+    HHG_CHECK(cfg >= -2 && cfg < SMOOTH32_CONFIGS, HHG_EINVAL, "unknown smoother configuration");
     s->levels[n].tune32 = cfg;
     ++s->gen;
   });

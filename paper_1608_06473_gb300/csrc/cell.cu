@@ -7,22 +7,29 @@
 // precision, because GB300 issues FP64 at a small fraction of its FP32 and
 // INT32 rate:
 //
-//  * FP64: the line polynomials of every cell are computed once per fit
-//    (lsqp_line_table_kernel) as integers scaled by 2^E (E per cell, chosen so
-//    every partial sum stays below 2^62) and kept in HBM.  Per node the
-//    polynomial is evaluated exactly by integer Horner and converted to FP64
-//    on the integer pipe; the FP64 pipe carries only the 14 stencil products,
-//    the scaling and a Newton-Raphson divide.  Kernels are thread-per-node
-//    with one CTA per macro cell and no barriers; the smoother is one launch
-//    per colour.
+//  * FP64: per plane k each direction's polynomial is reduced to a
+//    polynomial in (i, j) at fit time and stored as integers scaled by 2^E
+//    (E per cell, chosen so every partial sum stays below 2^61): 15 m
+//    numbers per plane with m = (q+1)(q+2)/2, 44 KB per cell at q = 2,
+//    N = 64.  A CTA stages its cell's table in shared memory, and every node
+//    evaluates its weights exactly by integer Horner in j and i, converts
+//    them on the integer pipe, and forms the reciprocal of its centre weight
+//    on the integer pipe too; the FP64 pipe carries only the 14 stencil
+//    products and one multiply.  Kernels are thread-per-node with one CTA per
+//    macro cell and no barriers after the staging; the smoother is one
+//    launch per colour.
 //  * FP32: per plane k each direction's polynomial is reduced to a
 //    polynomial in (i, j) at fit time (FP32 table) and evaluated per node
 //    from shared memory, thread per node, one launch per colour.  The
-//    smoother may instead run as the shared-memory staged one-launch sweep
-//    of stage.cu; a tuner times both per level and picks (lv.smooth_cfg).
+//    smoother may instead run as a one-launch sweep per cell: the plane
+//    wavefront of wave.cu or the shared-memory staged sweep of stage.cu; a
+//    tuner times the candidates per level and picks one (lv.smooth_cfg).
 //
 // IFEM (Sec. 4.2.1): every node assembles its 15 weights from the 24 element
 // matrices around it (thread per node, one launch per colour).
+//
+// Batched right-hand sides: persistent kernels (grid-stride over cells) that
+// form a node's weights once and apply them to every vector.
 //
 // Neighbour addressing: nodes whose 14 neighbours are all interior use
 // closed-form 32-bit offsets within the cell's block of the canonical
@@ -32,6 +39,7 @@
 
 #include <cuda_runtime.h>
 
+#include "arith.cuh"
 #include "device.cuh"
 #include "kernels.h"
 
@@ -47,39 +55,6 @@ constexpr int NODE64_THREADS = 512;
 // FP32 surrogate kernel: 512 threads x 2 CTAs per SM measured 4% (N = 64) and
 // 14% (N = 128) faster than 256 x 4 on GB300.
 constexpr int NODE32_THREADS = 512;
-
-// Coefficients of the polynomial in i along line (j, k): c_a(j, k) =
-// sum_{b,d} A_{a,b,d} j^b k^d.  Storage order of A (per direction):
-// for a = 0..Q, for d = 0..Q-a, for b = 0..Q-a-d.
-template <class T, int Q>
-__device__ __forceinline__ void line_coeffs(const T* A, T j, T k, T* out) {
-  int t = 0;
-#pragma unroll
-  for (int a = 0; a <= Q; ++a) {
-    T inner[Q + 1];
-#pragma unroll
-    for (int d = 0; d <= Q - a; ++d) {
-      const int n = Q - a - d + 1;
-      T v = A[t + n - 1];
-#pragma unroll
-      for (int b = n - 2; b >= 0; --b) v = fma(v, j, A[t + b]);
-      inner[d] = v;
-      t += n;
-    }
-    T ca = inner[Q - a];
-#pragma unroll
-    for (int d = Q - a - 1; d >= 0; --d) ca = fma(ca, k, inner[d]);
-    out[a] = ca;
-  }
-}
-
-template <class T, int Q>
-__device__ __forceinline__ T eval_line(const T* cl, T i) {
-  T v = cl[Q];
-#pragma unroll
-  for (int a = Q - 1; a >= 0; --a) v = fma(v, i, cl[a]);
-  return v;
-}
 
 // Stencil application at one interior node.  wt(w) returns weight w (the
 // centre is w = MC), possibly scaled by 2^E; `scale` = 2^E, `inv_scale` =
@@ -127,26 +102,71 @@ __device__ __forceinline__ void node_update(const LevelView<T>& lv, int c, int i
   }
 }
 
-// Right-hand sides per batched launch: the weights of a node are evaluated
-// once and applied to RB vectors.
-constexpr int RB = 4;
+// ---------------------------------------------------------------------------
+// Batched right-hand sides: a node's 15 weights (and, for the smoother, the
+// reciprocal of its centre weight) are formed once and applied to all
+// lv.nrhs vectors.  Residual norms accumulate per thread and right-hand side
+// in shared memory (s_nrm[b blockDim + thread]) and are summed per cell.
+// ---------------------------------------------------------------------------
+template <class T, Mode MODE>
+__device__ __forceinline__ void node_apply_all(const LevelView<T>& lv, int c, int i, int j, int k, const T (&w)[15],
+                                               T rc, T* u, T* out, const T* f, double* s_nrm) {
+  const int64_t cb = lv.off_C + (int64_t)c * lv.n_int;
+  const int64_t I = cb + lin_interior32(i, j, k, lv.N);
+  const bool deep = deep_interior(i, j, k, lv.N);
+  int off[14];
+  if (deep) neighbour_offsets(j, k, lv.N, off);
+  for (int b = 0; b < lv.nrhs; ++b) {
+    T* ub = u + (int64_t)b * lv.vstride;
+    const T* gb = lv.ghost + (int64_t)b * lv.gstride;
+    auto nb = [&](int v) -> T {
+      if (deep) return ub[I + off[v]];
+      const int i2 = i + DI(v), j2 = j + DJ(v), k2 = k + DK(v);
+      if (is_interior(i2, j2, k2, lv.N)) return ub[cb + lin_interior32(i2, j2, k2, lv.N)];
+      return gb[(int64_t)c * lv.n_full + lin_full(i2, j2, k2, lv.N)];
+    };
+    if (MODE == SMOOTH) {
+      T acc = f[(int64_t)b * lv.vstride + I];
+#pragma unroll
+      for (int v = 0; v < 14; ++v) acc = fma(-w[v], nb(v), acc);
+      ub[I] = acc * rc;
+    } else {
+      T y = w[MC] * ub[I];
+#pragma unroll
+      for (int v = 0; v < 14; ++v) y = fma(w[v], nb(v), y);
+      if (MODE == APPLY) {
+        out[(int64_t)b * lv.vstride + I] = y;
+      } else {
+        const T r = f[(int64_t)b * lv.vstride + I] - y;
+        out[(int64_t)b * lv.vstride + I] = r;
+        double& acc = s_nrm[b * blockDim.x + threadIdx.x];
+        acc = fma((double)r, (double)r, acc);
+      }
+    }
+  }
+}
 
-// The update of node (i, j, k) of cell c for right-hand sides b0 .. b0+G-1
-// (G <= RB) with its 15 weights w[] already evaluated.  CHAIN: one FMA chain
-// in direction order and the Newton-Raphson divide (the FP64 surrogate
-// kernel's arithmetic); otherwise node_update's two-accumulator form.
-template <class T, Mode MODE, bool CHAIN, class W>
-__device__ __forceinline__ void node_update_batch(const LevelView<T>& lv, int c, int i, int j, int k, const W* w,
-                                                  T* u, T* out, const T* f, double (&nrm)[RB], int b0, int G,
-                                                  T scale, T inv_scale);
+// Per-right-hand-side sums of the shared-memory norm accumulators of cell c.
+__device__ __forceinline__ void batch_norms_out(const double* s_nrm, int nrhs, int pstride, int c, double* partial) {
+  for (int b = 0; b < nrhs; ++b) {
+    const double tot = block_sum(s_nrm[b * blockDim.x + threadIdx.x]);
+    if (threadIdx.x == 0) partial[(int64_t)b * pstride + c] = tot;
+  }
+}
 
 // ---------------------------------------------------------------------------
-// FP64 surrogate: line table at fit time, thread-per-node application
+// FP64 surrogate: integer plane table at fit time, staged per cell in shared
+// memory; thread-per-node application
 // ---------------------------------------------------------------------------
 
-// E per cell: B = max_w sum_t |A_wt| N^deg(t) bounds |c_a(j,k)| i^a on every
-// line and node, so with B 2^E < 2^60 every Horner partial sum of
-// C_q i^q + .. + C_0 stays below (q + 1) 2^60 <= 2^62.
+template <int Q>
+constexpr int NPP64 = ((Q + 1) * (Q + 2) / 2 + 1) / 2 * 2;
+
+// E per cell: B = max_w sum_t |A_wt| N^deg(t) bounds every partial sum of
+// the nested Horner evaluation (in j, then in i) of any direction's
+// polynomial at any node, so with B 2^E < 2^60 every partial sum of the
+// integer evaluation stays below 2^61 (the rounded plane coefficients add at
+// most (q + 1)(q + 2) N^q / 4).
 template <int Q>
 __global__ void lsqp_scale_kernel(const double* __restrict__ coef, int nC, int N, int* __restrict__ cell_e) {
   constexpr int MQ = (Q + 1) * (Q + 2) * (Q + 3) / 6;
@@ -166,268 +186,152 @@ __global__ void lsqp_scale_kernel(const double* __restrict__ coef, int nC, int N
   cell_e[c] = 60 - (ilogb(B > 0.0 ? B : 1.0) + 1);
 }
 
+// Plane table: for cell c, plane k and direction w, D_ab(k) = sum_d A_abd k^d
+// (FP64) times 2^E, rounded to int64, NPP64 values per direction.
 template <int Q>
-__global__ void lsqp_line_table_kernel(const double* __restrict__ coef, const int* __restrict__ cell_e, int nC, int N,
-                                       long long* __restrict__ table) {
+__global__ void lsqp_plane64_kernel(const double* __restrict__ coef, const int* __restrict__ cell_e, int nC, int N,
+                                    long long* __restrict__ table) {
   constexpr int MQ = (Q + 1) * (Q + 2) * (Q + 3) / 6;
-  const int nl = (int)n_cell_lines(N);
+  constexpr int NP = (Q + 1) * (Q + 2) / 2;
+  const int np = N - 3;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)nC * nl) return;
-  const int c = (int)(t / nl), line = (int)(t % nl);
-  int k = 1, j = line + 1;
-  while (j > N - 2 - k) {
-    j -= N - 2 - k;
-    ++k;
-  }
+  if (t >= (int64_t)nC * np * 15) return;
+  const int w = (int)(t % 15);
+  const int64_t cp = t / 15;
+  const int c = (int)(cp / np), k = (int)(cp % np) + 1;
+  double P[NP];
+  plane_coeffs<double, Q>(coef + ((int64_t)c * 15 + w) * MQ, (double)k, P);
   const double sc = ldexp(1.0, cell_e[c]);
-  long long* dst = table + t * line_rec(Q);
-  for (int w = 0; w < 15; ++w) {
-    double cl[Q + 1];
-    line_coeffs<double, Q>(coef + ((int64_t)c * 15 + w) * MQ, (double)j, (double)k, cl);
+  long long* dst = table + t * NPP64<Q>;
 #pragma unroll
-    for (int a = 0; a <= Q; ++a) dst[w * (Q + 1) + a] = __double2ll_rn(cl[a] * sc);
-  }
-  for (int r = 15 * (Q + 1); r < line_rec(Q); ++r) dst[r] = 0;
+  for (int a = 0; a < NPP64<Q>; ++a) dst[a] = a < NP ? __double2ll_rn(P[a] * sc) : 0ll;
 }
 
-// v * i + c (mod 2^64) for a 32-bit multiplier i >= 0: the low word times i
-// widened to 64 bits plus c, then the high word times i added to the top
-// half (two integer multiply-adds instead of a full 64 x 64 product).
-__device__ __forceinline__ long long mad_i64_u32(long long v, unsigned i, long long c) {
-  const unsigned long long vu = (unsigned long long)v;
-  unsigned long long r = (unsigned long long)(unsigned)vu * i + (unsigned long long)c;
-  r += (unsigned long long)((unsigned)(vu >> 32) * i) << 32;
-  return (long long)r;
-}
-
-// Line polynomial C_Q i^Q + ... + C_0 in exact integer arithmetic (Horner).
+// The polynomial of one direction in (i, j) evaluated exactly in integer
+// arithmetic: Horner in j for each power of i, then Horner in i (the same
+// nesting as eval_plane).  P: NPP64 int64 in shared memory.
 template <int Q>
-__device__ __forceinline__ long long horner_i64(const long long* C, unsigned i) {
-  long long v = C[Q];
+__device__ __forceinline__ long long eval_plane_i64(const long long* P, unsigned i, unsigned j) {
+  long long r[NPP64<Q>];
 #pragma unroll
-  for (int a = Q - 1; a >= 0; --a) v = mad_i64_u32(v, i, C[a]);
-  return v;
+  for (int h = 0; h < NPP64<Q> / 2; ++h) {
+    const longlong2 x = reinterpret_cast<const longlong2*>(P)[h];
+    r[2 * h] = x.x;
+    r[2 * h + 1] = x.y;
+  }
+  long long s = 0;
+#pragma unroll
+  for (int a = Q; a >= 0; --a) {
+    long long c = r[plane_index<Q>(a, Q - a)];
+#pragma unroll
+    for (int b = Q - a - 1; b >= 0; --b) c = mad_i64_u32(c, j, r[plane_index<Q>(a, b)]);
+    s = (a == Q) ? c : mad_i64_u32(s, i, c);
+  }
+  return s;
 }
 
-// int64 -> FP64 on the integer pipe (GB300 issues FP64 conversions on its
-// narrow FP64 pipe): magnitude, leading-zero count, normalising shift, and
-// the biased exponent added to the top bits, where the leading one of the
-// shifted magnitude carries into the exponent field.  The mantissa is
-// truncated toward zero (relative error below 2^-52); 0 maps to +0.
-__device__ __forceinline__ double i64_to_f64(long long v) {
-  const unsigned long long sign = (unsigned long long)v & 0x8000000000000000ull;
-  const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
-  const int lz = __clzll((long long)a);
-  unsigned long long m;
-  asm("shl.b64 %0, %1, %2;" : "=l"(m) : "l"(a), "r"(lz));  // PTX clamps a shift of 64 to 0
-  const unsigned long long bits = ((unsigned long long)(1085 - lz) << 52) + (m >> 11);
-  return a ? __longlong_as_double((long long)(bits | sign)) : 0.0;
+// Cell c's plane table into shared memory (16-byte loads).
+template <int Q>
+__device__ __forceinline__ void load_plane64(const LevelView<double>& lv, int c, long long* s_tab) {
+  const int n2 = (lv.N - 3) * 15 * NPP64<Q> / 2;
+  const longlong2* src = reinterpret_cast<const longlong2*>(lv.plane64 + (int64_t)c * 2 * n2);
+  longlong2* dst = reinterpret_cast<longlong2*>(s_tab);
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) dst[t] = __ldg(src + t);
 }
 
-// n / d for normal d: the hardware reciprocal estimate refined by two
-// Newton-Raphson steps x <- x + x (1 - d x) (each squares the relative error),
-// the last one folded into the product: n x (1 + e) with e = 1 - d x.  The
-// result is within a few ulp of the correctly rounded quotient, at 5 FP64
-// operations instead of the longer IEEE division sequence.
-__device__ __forceinline__ double div_nr(double n, double d) {
-  double x;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(d));
-  double e = fma(-d, x, 1.0);
-  x = fma(x, e, x);
-  e = fma(-d, x, 1.0);
-  const double t = n * x;
-  return fma(t, e, t);
-}
-
-// One interior node of the FP64 surrogate.  C is the line record of (j, k):
-// 15 polynomials in i of degree Q, Q + 1 int64 each, scaled by 2^E.  Weights
-// are formed in pairs (w, w + 1) from 16-byte loads (the pair starts at an
-// even int64 offset) and converted on the integer pipe; the FP64 pipe
-// carries only the 14 products, the scaling and the divide.
+// One interior node of the FP64 surrogate.  P: the node's plane in shared
+// memory (15 directions x NPP64 int64, scaled by 2^E).  Every weight is
+// evaluated exactly on the integer pipe and converted with the scale undone
+// (i64_to_f64_scaled); the smoother's divide by the centre weight is a
+// product with its reciprocal, also formed on the integer pipe
+// (rcp_i64_scaled).  The FP64 pipe carries only the 14 products and that
+// one multiply (15 operations per update).
 template <int Q, Mode MODE, class NB>
-__device__ __forceinline__ void lsqp64_node(const long long* __restrict__ C, unsigned i, NB nb, int64_t I, double* u,
-                                            double* out, const double* f, double& nrm, double scale,
-                                            double inv_scale) {
-  auto pair = [&](int w, double& a, double& b) {
-    long long r[2 * (Q + 1)];
-    const longlong2* p2 = reinterpret_cast<const longlong2*>(C + w * (Q + 1));
-#pragma unroll
-    for (int h = 0; h < Q + 1; ++h) {
-      const longlong2 x = __ldg(p2 + h);
-      r[2 * h] = x.x;
-      r[2 * h + 1] = x.y;
-    }
-    a = i64_to_f64(horner_i64<Q>(r, i));
-    b = i64_to_f64(horner_i64<Q>(r + Q + 1, i));
-  };
-  auto centre = [&]() {
-    long long r[Q + 2];
-    const longlong2* p2 = reinterpret_cast<const longlong2*>(C + MC * (Q + 1));
-#pragma unroll
-    for (int h = 0; h < (Q + 2) / 2; ++h) {
-      const longlong2 x = __ldg(p2 + h);
-      r[2 * h] = x.x;
-      r[2 * h + 1] = x.y;
-    }
-    return i64_to_f64(horner_i64<Q>(r, i));
-  };
+__device__ __forceinline__ void lsqp64_node(const long long* P, unsigned i, unsigned j, int E, NB nb, int64_t I,
+                                            double* u, double* out, const double* f, double& nrm) {
+  auto wt = [&](int w) { return i64_to_f64_scaled(eval_plane_i64<Q>(P + w * NPP64<Q>, i, j), E); };
   if (MODE == SMOOTH) {
-    double acc = f[I] * scale;
+    double acc = f[I];
 #pragma unroll
-    for (int w = 0; w < 14; w += 2) {
-      double a, b;
-      pair(w, a, b);
-      acc = fma(-a, nb(w), acc);
-      acc = fma(-b, nb(w + 1), acc);
-    }
-    u[I] = div_nr(acc, centre());
+    for (int w = 0; w < 14; ++w) acc = fma(-wt(w), nb(w), acc);
+    u[I] = acc * rcp_i64_scaled(eval_plane_i64<Q>(P + MC * NPP64<Q>, i, j), E);
   } else {
-    double y = centre() * u[I];
+    double y = wt(MC) * u[I];
 #pragma unroll
-    for (int w = 0; w < 14; w += 2) {
-      double a, b;
-      pair(w, a, b);
-      y = fma(a, nb(w), y);
-      y = fma(b, nb(w + 1), y);
-    }
+    for (int w = 0; w < 14; ++w) y = fma(wt(w), nb(w), y);
     if (MODE == APPLY) {
-      out[I] = y * inv_scale;
+      out[I] = y;
     } else {
-      const double r = fma(-inv_scale, y, f[I]);
+      const double r = f[I] - y;
       out[I] = r;
       nrm = fma(r, r, nrm);
     }
   }
 }
 
-template <class T, Mode MODE, bool CHAIN, class W>
-__device__ __forceinline__ void node_update_batch(const LevelView<T>& lv, int c, int i, int j, int k, const W* w,
-                                                  T* u, T* out, const T* f, double (&nrm)[RB], int b0, int G,
-                                                  T scale, T inv_scale) {
-  const int64_t I = lv.off_C + (int64_t)c * lv.n_int + lin_interior32(i, j, k, lv.N);
-  const bool deep = deep_interior(i, j, k, lv.N);
-  int off[14];
-  if (deep) neighbour_offsets(j, k, lv.N, off);
-#pragma unroll
-  for (int g = 0; g < RB; ++g) {
-    if (g >= G) break;
-    const int64_t b = b0 + g;
-    T* ub = u + b * lv.vstride;
-    const T* gb = lv.ghost + b * lv.gstride;
-    auto nb = [&](int v) -> T {
-      if (deep) return ub[I + off[v]];
-      const int i2 = i + DI(v), j2 = j + DJ(v), k2 = k + DK(v);
-      if (is_interior(i2, j2, k2, lv.N)) return ub[lv.off_C + (int64_t)c * lv.n_int + lin_interior32(i2, j2, k2, lv.N)];
-      return gb[(int64_t)c * lv.n_full + lin_full(i2, j2, k2, lv.N)];
-    };
-    if (MODE == SMOOTH) {
-      const T fb = f[b * lv.vstride + I];
-      if (CHAIN) {
-        T acc = fb * scale;
-#pragma unroll
-        for (int v = 0; v < 14; ++v) acc = fma(-(T)w[v], nb(v), acc);
-        ub[I] = (T)div_nr((double)acc, (double)w[MC]);
-      } else {
-        T a0 = fb * scale, a1 = 0;
-#pragma unroll
-        for (int v = 0; v < 14; v += 2) {
-          a0 = fma(-(T)w[v], nb(v), a0);
-          a1 = fma(-(T)w[v + 1], nb(v + 1), a1);
-        }
-        ub[I] = (a0 + a1) / (T)w[MC];
-      }
-    } else {
-      T y;
-      if (CHAIN) {
-        y = (T)w[MC] * ub[I];
-#pragma unroll
-        for (int v = 0; v < 14; ++v) y = fma((T)w[v], nb(v), y);
-      } else {
-        T a0 = (T)w[MC] * ub[I], a1 = 0;
-#pragma unroll
-        for (int v = 0; v < 14; v += 2) {
-          a0 = fma((T)w[v], nb(v), a0);
-          a1 = fma((T)w[v + 1], nb(v + 1), a1);
-        }
-        y = a0 + a1;
-      }
-      if (MODE == APPLY) {
-        out[b * lv.vstride + I] = y * inv_scale;
-      } else {
-        const T r = fma(-inv_scale, y, f[b * lv.vstride + I]);
-        out[b * lv.vstride + I] = r;
-        nrm[g] = CHAIN ? fma((double)r, (double)r, nrm[g]) : nrm[g] + (double)r * (double)r;
-      }
-    }
-  }
-}
-
-// Per-right-hand-side block sums of a batched residual into partial.
-__device__ __forceinline__ void batch_partials(const double (&nrm)[RB], int b0, int G, int pstride, int c,
-                                               double* partial) {
-#pragma unroll
-  for (int g = 0; g < RB; ++g) {
-    if (g >= G) break;
-    const double tot = block_sum(nrm[g]);
-    if (threadIdx.x == 0) partial[(int64_t)(b0 + g) * pstride + c] = tot;
-  }
-}
-
-// FP64 surrogate for RB right-hand sides at once: the 15 weights of a node
-// are formed once (integer pipe) and applied to every vector of the group.
-template <int Q, Mode MODE>
-__global__ void __launch_bounds__(NODE_THREADS, 2) lsqp_node_batch_kernel(LevelView<double> lv,
-                                                                          const uint32_t* __restrict__ list, int n_list,
-                                                                          double* u, double* out, const double* f,
-                                                                          double* partial, int b0, int G) {
-  const int c = blockIdx.x;
-  const int N = lv.N;
-  const int E = lv.cell_e[c];
-  const double scale = ldexp(1.0, E), inv_scale = ldexp(1.0, -E);
-  const long long* tab = lv.line64 + (int64_t)c * lv.n_lines * line_rec(Q);
-  double nrm[RB] = {};
-  for (int t = threadIdx.x; t < n_list; t += blockDim.x) {
-    const uint32_t p = list[t];
-    const int i = unpack_i(p), j = unpack_j(p), k = unpack_k(p);
-    const long long* C = tab + (int64_t)line_id(j, k, N) * line_rec(Q);
-    double w[15];
-#pragma unroll
-    for (int v = 0; v < 15; ++v) w[v] = i64_to_f64(horner_i64<Q>(C + v * (Q + 1), (unsigned)i));
-    node_update_batch<double, MODE, true>(lv, c, i, j, k, w, u, out, f, nrm, b0, G, scale, inv_scale);
-  }
-  if (MODE == RESIDUAL) batch_partials(nrm, b0, G, lv.pstride, c, partial);
-}
-
 template <int Q, Mode MODE>
 __global__ void __launch_bounds__(NODE64_THREADS, 2) lsqp_node_kernel(LevelView<double> lv, const uint32_t* __restrict__ list,
                                                                   int n_list, double* u, double* out, const double* f,
                                                                   double* partial) {
+  extern __shared__ __align__(16) long long s_tab64[];   // [N - 3][15][NPP64]
   const int c = blockIdx.x;
   const int N = lv.N;
+  load_plane64<Q>(lv, c, s_tab64);
   const int E = lv.cell_e[c];
-  const double scale = ldexp(1.0, E), inv_scale = ldexp(1.0, -E);
-  const long long* tab = lv.line64 + (int64_t)c * lv.n_lines * line_rec(Q);
   const int64_t base = lv.off_C + (int64_t)c * lv.n_int;
+  __syncthreads();
   double nrm = 0.0;
   for (int t = threadIdx.x; t < n_list; t += blockDim.x) {
     const uint32_t p = list[t];
     const int i = unpack_i(p), j = unpack_j(p), k = unpack_k(p);
-    const long long* C = tab + (int64_t)line_id(j, k, N) * line_rec(Q);
+    const long long* P = s_tab64 + (k - 1) * 15 * NPP64<Q>;
     const int64_t I = base + lin_interior32(i, j, k, N);
     if (deep_interior(i, j, k, N)) {
       int off[14];
       neighbour_offsets(j, k, N, off);
       const double* pu = u + I;
-      lsqp64_node<Q, MODE>(C, (unsigned)i, [&](int w) { return pu[off[w]]; }, I, u, out, f, nrm, scale, inv_scale);
+      lsqp64_node<Q, MODE>(P, (unsigned)i, (unsigned)j, E, [&](int w) { return pu[off[w]]; }, I, u, out, f, nrm);
     } else {
-      lsqp64_node<Q, MODE>(C, (unsigned)i,
+      lsqp64_node<Q, MODE>(P, (unsigned)i, (unsigned)j, E,
                            [&](int w) { return load_pt(lv, (const double*)u, c, i + DI(w), j + DJ(w), k + DK(w)); },
-                           I, u, out, f, nrm, scale, inv_scale);
+                           I, u, out, f, nrm);
     }
   }
   if (MODE == RESIDUAL) {
     const double tot = block_sum(nrm);
     if (threadIdx.x == 0) partial[c] = tot;
+  }
+}
+
+// FP64 surrogate for all lv.nrhs right-hand sides at once, persistent over
+// cells (grid-stride loop): per cell the plane table is staged once, per
+// node the 15 weights and the centre reciprocal are formed once.
+template <int Q, Mode MODE>
+__global__ void __launch_bounds__(NODE_THREADS, 2) lsqp_node_batch_kernel(LevelView<double> lv,
+                                                                          const uint32_t* __restrict__ list, int n_list,
+                                                                          double* u, double* out, const double* f,
+                                                                          double* partial) {
+  extern __shared__ __align__(16) long long s_tab64[];   // [N - 3][15][NPP64], then [nrhs][blockDim] doubles
+  const int N = lv.N;
+  double* s_nrm = reinterpret_cast<double*>(s_tab64 + (N - 3) * 15 * NPP64<Q>);
+  for (int c = blockIdx.x; c < lv.nC; c += gridDim.x) {
+    __syncthreads();
+    load_plane64<Q>(lv, c, s_tab64);
+    if (MODE == RESIDUAL)
+      for (int b = 0; b < lv.nrhs; ++b) s_nrm[b * blockDim.x + threadIdx.x] = 0.0;
+    const int E = lv.cell_e[c];
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_list; t += blockDim.x) {
+      const uint32_t p = list[t];
+      const int i = unpack_i(p), j = unpack_j(p), k = unpack_k(p);
+      const long long* P = s_tab64 + (k - 1) * 15 * NPP64<Q>;
+      double w[15];
+#pragma unroll
+      for (int v = 0; v < 15; ++v) w[v] = i64_to_f64_scaled(eval_plane_i64<Q>(P + v * NPP64<Q>, i, j), E);
+      const double rc = MODE == SMOOTH ? rcp_i64_scaled(eval_plane_i64<Q>(P + MC * NPP64<Q>, i, j), E) : 0.0;
+      node_apply_all<double, MODE>(lv, c, i, j, k, w, rc, u, out, f, s_nrm);
+    }
+    if (MODE == RESIDUAL) batch_norms_out(s_nrm, lv.nrhs, lv.pstride, c, partial);
   }
 }
 
@@ -594,36 +498,42 @@ __global__ void __launch_bounds__(NODE_THREADS, 4) lsqp_node32_x2_kernel(LevelVi
   }
 }
 
-// FP32 surrogate for RB right-hand sides at once (weights evaluated once per
-// node from the per-plane table in shared memory).
+// FP32 surrogate for all lv.nrhs right-hand sides at once, persistent over
+// cells: per cell the per-plane table is staged once, per node the 15
+// weights (5 FMA each from the table) and the centre reciprocal are formed
+// once and applied to every vector.
 template <int Q, Mode MODE>
 __global__ void __launch_bounds__(NODE_THREADS, 2) lsqp_node32_batch_kernel(LevelView<float> lv,
                                                                             const uint32_t* __restrict__ list,
                                                                             int n_list, float* u, float* out,
-                                                                            const float* f, double* partial, int b0,
-                                                                            int G) {
+                                                                            const float* f, double* partial) {
   constexpr int NP = (Q + 1) * (Q + 2) / 2;
   constexpr int NPP = np_pad<Q>();
-  extern __shared__ __align__(16) float s_tab[];   // [N - 3][15][NPP]
-  const int c = blockIdx.x;
+  extern __shared__ __align__(16) float s_tab[];   // [N - 3][15][NPP], then [nrhs][blockDim] doubles
   const int np = lv.N - 3;
-  const float* tab = lv.plane32 + (int64_t)c * np * 15 * NP;
-  for (int t = threadIdx.x; t < np * 15 * NPP; t += blockDim.x) {
-    const int e = t % NPP, pw = t / NPP;
-    s_tab[t] = e < NP ? tab[pw * NP + e] : 0.0f;
-  }
-  __syncthreads();
-  double nrm[RB] = {};
-  for (int t = threadIdx.x; t < n_list; t += blockDim.x) {
-    const uint32_t p = list[t];
-    const int i = unpack_i(p), j = unpack_j(p), k = unpack_k(p);
-    const float* P = s_tab + (k - 1) * 15 * NPP;
-    float w[15];
+  double* s_nrm = reinterpret_cast<double*>(s_tab + np * 15 * NPP);
+  for (int c = blockIdx.x; c < lv.nC; c += gridDim.x) {
+    __syncthreads();
+    const float* tab = lv.plane32 + (int64_t)c * np * 15 * NP;
+    for (int t = threadIdx.x; t < np * 15 * NPP; t += blockDim.x) {
+      const int e = t % NPP, pw = t / NPP;
+      s_tab[t] = e < NP ? tab[pw * NP + e] : 0.0f;
+    }
+    if (MODE == RESIDUAL)
+      for (int b = 0; b < lv.nrhs; ++b) s_nrm[b * blockDim.x + threadIdx.x] = 0.0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_list; t += blockDim.x) {
+      const uint32_t p = list[t];
+      const int i = unpack_i(p), j = unpack_j(p), k = unpack_k(p);
+      const float* P = s_tab + (k - 1) * 15 * NPP;
+      float w[15];
 #pragma unroll
-    for (int v = 0; v < 15; ++v) w[v] = eval_plane<float, Q>(P + v * NPP, (float)i, (float)j);
-    node_update_batch<float, MODE, false>(lv, c, i, j, k, w, u, out, f, nrm, b0, G, 1.0f, 1.0f);
+      for (int v = 0; v < 15; ++v) w[v] = eval_plane<float, Q>(P + v * NPP, (float)i, (float)j);
+      const float rc = MODE == SMOOTH ? 1.0f / w[MC] : 0.0f;
+      node_apply_all<float, MODE>(lv, c, i, j, k, w, rc, u, out, f, s_nrm);
+    }
+    if (MODE == RESIDUAL) batch_norms_out(s_nrm, lv.nrhs, lv.pstride, c, partial);
   }
-  if (MODE == RESIDUAL) batch_partials(nrm, b0, G, lv.pstride, c, partial);
 }
 
 // ---------------------------------------------------------------------------
@@ -654,47 +564,95 @@ __global__ void __launch_bounds__(NODE_THREADS) ifem_node_kernel(LevelView<T> lv
   }
 }
 
-// IFEM for RB right-hand sides at once (one stencil assembly per node).
+// IFEM for all lv.nrhs right-hand sides at once, persistent over cells: one
+// stencil assembly per node, applied to every vector.
 template <class T, Mode MODE>
 __global__ void __launch_bounds__(NODE_THREADS) ifem_node_batch_kernel(LevelView<T> lv, const uint32_t* __restrict__ list,
                                                                         int n_list, T* u, T* out, const T* f,
-                                                                        double* partial, int b0, int G) {
+                                                                        double* partial) {
   __shared__ CellGeom g;
-  const int c = blockIdx.x;
-  if (threadIdx.x < 16)
-    reinterpret_cast<double*>(&g)[threadIdx.x] = reinterpret_cast<const double*>(&lv.geom[c])[threadIdx.x];
-  __syncthreads();
-  double nrm[RB] = {};
-  for (int t = threadIdx.x; t < n_list; t += blockDim.x) {
-    const uint32_t p = list[t];
-    const int i = unpack_i(p), j = unpack_j(p), k = unpack_k(p);
-    double s[15];
-    ifem_stencil(g, lv.N, i, j, k, s);
-    node_update_batch<T, MODE, false>(lv, c, i, j, k, s, u, out, f, nrm, b0, G, T(1), T(1));
+  extern __shared__ __align__(16) double s_nrm_ifem[];   // [nrhs][blockDim]
+  for (int c = blockIdx.x; c < lv.nC; c += gridDim.x) {
+    __syncthreads();
+    if (threadIdx.x < 16)
+      reinterpret_cast<double*>(&g)[threadIdx.x] = reinterpret_cast<const double*>(&lv.geom[c])[threadIdx.x];
+    if (MODE == RESIDUAL)
+      for (int b = 0; b < lv.nrhs; ++b) s_nrm_ifem[b * blockDim.x + threadIdx.x] = 0.0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_list; t += blockDim.x) {
+      const uint32_t p = list[t];
+      const int i = unpack_i(p), j = unpack_j(p), k = unpack_k(p);
+      double s[15];
+      ifem_stencil(g, lv.N, i, j, k, s);
+      T w[15];
+#pragma unroll
+      for (int v = 0; v < 15; ++v) w[v] = (T)s[v];
+      const T rc = MODE == SMOOTH ? (T)(1.0 / s[MC]) : T(0);
+      node_apply_all<T, MODE>(lv, c, i, j, k, w, rc, u, out, f, s_nrm_ifem);
+    }
+    if (MODE == RESIDUAL) batch_norms_out(s_nrm_ifem, lv.nrhs, lv.pstride, c, partial);
   }
-  if (MODE == RESIDUAL) batch_partials(nrm, b0, G, lv.pstride, c, partial);
 }
 
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 
+// Largest dynamic shared memory a batched launch plans for (the device
+// allows 227 KB per CTA; the rest is left to static shared memory).
+constexpr size_t SMEM_BATCH_MAX = 220 * 1024;
+
+// Grid of a persistent kernel: as many CTAs as are resident at once, at most nC.
+int persistent_grid(const void* kern, int threads, size_t smem, int nC) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    HHG_CUDA(cudaGetDevice(&dev));
+    HHG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  int per = 0;
+  HHG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem));
+  return std::max(1, std::min(nC, sms * std::max(per, 1)));
+}
+
+// A batched cell kernel over all lv.nrhs right-hand sides.  In RESIDUAL mode
+// the per-thread norm accumulators (nrhs x NODE_THREADS doubles) follow the
+// table in shared memory, so right-hand sides go in chunks that fit.
+template <class T, Mode MODE, class K>
+void launch_batch(K kern, const LevelView<T>& lv, size_t table_bytes, const uint32_t* list, int n, T* u, T* out,
+                  const T* f, double* partial, cudaStream_t st) {
+  const size_t per_rhs = MODE == RESIDUAL ? sizeof(double) * NODE_THREADS : 0;
+  HHG_CHECK(table_bytes + per_rhs <= SMEM_BATCH_MAX, HHG_EINVAL, "batched cell kernel: table exceeds shared memory");
+  const int chunk = per_rhs ? (int)std::min<size_t>(lv.nrhs, (SMEM_BATCH_MAX - table_bytes) / per_rhs) : lv.nrhs;
+  for (int b0 = 0; b0 < lv.nrhs; b0 += chunk) {
+    LevelView<T> sub = lv;
+    sub.nrhs = std::min(chunk, lv.nrhs - b0);
+    sub.ghost = lv.ghost + (int64_t)b0 * lv.gstride;
+    const int64_t vo = (int64_t)b0 * lv.vstride;
+    const size_t smem = table_bytes + per_rhs * sub.nrhs;
+    ensure_smem_limit((const void*)kern, smem);
+    const int grid = persistent_grid((const void*)kern, NODE_THREADS, smem, lv.nC);
+    kern<<<grid, NODE_THREADS, smem, st>>>(sub, list, n, u + vo, out ? out + vo : nullptr, f ? f + vo : nullptr,
+                                           partial ? partial + (int64_t)b0 * lv.pstride : nullptr);
+    HHG_CUDA(cudaGetLastError());
+    count_launch();
+  }
+}
+
 template <int Q, Mode MODE>
 void launch_node64(const LevelView<double>& lv, const uint32_t* list, int n, double* u, double* out, const double* f,
                    double* partial, cudaStream_t st) {
-  HHG_CHECK(lv.line64 != nullptr, HHG_ENOTFIT, "FP64 surrogate line table missing");
+  HHG_CHECK(lv.plane64 != nullptr, HHG_ENOTFIT, "FP64 surrogate plane table missing");
+  const size_t table = sizeof(long long) * (size_t)(lv.N - 3) * 15 * NPP64<Q>;
   if (lv.nrhs == 1) {
-    lsqp_node_kernel<Q, MODE><<<lv.nC, NODE64_THREADS, 0, st>>>(lv, list, n, u, out, f, partial);
+    auto kern = lsqp_node_kernel<Q, MODE>;
+    ensure_smem_limit((const void*)kern, table);
+    kern<<<lv.nC, NODE64_THREADS, table, st>>>(lv, list, n, u, out, f, partial);
     HHG_CUDA(cudaGetLastError());
     count_launch();
     return;
   }
-  for (int b0 = 0; b0 < lv.nrhs; b0 += RB) {
-    lsqp_node_batch_kernel<Q, MODE><<<lv.nC, NODE_THREADS, 0, st>>>(lv, list, n, u, out, f, partial, b0,
-                                                                    std::min(RB, lv.nrhs - b0));
-    HHG_CUDA(cudaGetLastError());
-    count_launch();
-  }
+  launch_batch<double, MODE>(lsqp_node_batch_kernel<Q, MODE>, lv, table, list, n, u, out, f, partial, st);
 }
 
 template <int Q>
@@ -724,13 +682,7 @@ void launch_node32(const LevelView<float>& lv, const uint32_t* list, int n, floa
     count_launch();
     return;
   }
-  auto kern = lsqp_node32_batch_kernel<Q, MODE>;
-  ensure_smem_limit((const void*)kern, smem);
-  for (int b0 = 0; b0 < lv.nrhs; b0 += RB) {
-    kern<<<lv.nC, NODE_THREADS, smem, st>>>(lv, list, n, u, out, f, partial, b0, std::min(RB, lv.nrhs - b0));
-    HHG_CUDA(cudaGetLastError());
-    count_launch();
-  }
+  launch_batch<float, MODE>(lsqp_node32_batch_kernel<Q, MODE>, lv, smem, list, n, u, out, f, partial, st);
 }
 
 template <int Q>
@@ -756,12 +708,7 @@ void launch_ifem(const LevelView<T>& lv, const uint32_t* list, int n, T* u, T* o
     count_launch();
     return;
   }
-  for (int b0 = 0; b0 < lv.nrhs; b0 += RB) {
-    ifem_node_batch_kernel<T, MODE><<<lv.nC, NODE_THREADS, 0, st>>>(lv, list, n, u, out, f, partial, b0,
-                                                                    std::min(RB, lv.nrhs - b0));
-    HHG_CUDA(cudaGetLastError());
-    count_launch();
-  }
+  launch_batch<T, MODE>(ifem_node_batch_kernel<T, MODE>, lv, 0, list, n, u, out, f, partial, st);
 }
 
 template <class T>
@@ -844,15 +791,11 @@ void launch_cell<float>(const LevelView<float>& lv, int op, Mode mode, float* u,
                         double* partial, cudaStream_t st) {
   if (lv.N < 4 || lv.n_int == 0) return;
   if (op == HHG_OP_LSQP && lv.q > 0) {
-    if (mode == SMOOTH && lv.smooth_cfg >= 0 && stage32_supported(lv, u, lv.smooth_cfg) &&
-        (lv.nrhs == 1 || (lv.vstride % 4) == 0)) {
-      // one launch per right-hand side (the plane ring holds one vector)
-      for (int b = 0; b < lv.nrhs; ++b) {
-        LevelView<float> one = lv;
-        one.nrhs = 1;
-        one.ghost = lv.ghost + b * lv.gstride;
-        launch_stage32_smooth(one, u + b * lv.vstride, f + b * lv.vstride, lv.smooth_cfg, st);
-      }
+    // the staged sweep holds one vector's planes; batches take the batched
+    // per-colour kernel, which forms every node's weights once for all of them
+    if (mode == SMOOTH && lv.nrhs == 1 && lv.smooth_cfg >= 0 && smooth32_supported(lv, u, lv.smooth_cfg)) {
+      if (lv.smooth_cfg < STAGE32_CONFIGS) launch_stage32_smooth(lv, u, f, lv.smooth_cfg, st);
+      else launch_wave32_smooth(lv, u, f, lv.smooth_cfg - STAGE32_CONFIGS, st);
       return;
     }
     switch (lv.q) {
@@ -866,22 +809,22 @@ void launch_cell<float>(const LevelView<float>& lv, int op, Mode mode, float* u,
   ifem_all<float>(lv, mode, u, out, f, partial, st);
 }
 
-void launch_line_table(const LevelView<double>& lv, int q, const double* coef, int* cell_e, long long* table,
-                       cudaStream_t st) {
-  const int64_t n = (int64_t)lv.nC * n_cell_lines(lv.N);
+void launch_plane64_table(const LevelView<double>& lv, int q, const double* coef, int* cell_e, long long* table,
+                          cudaStream_t st) {
+  const int64_t n = (int64_t)lv.nC * (lv.N - 3) * 15;
   const unsigned gs = (unsigned)((lv.nC + 127) / 128), gl = (unsigned)((n + 127) / 128);
   switch (q) {
     case 1:
       lsqp_scale_kernel<1><<<gs, 128, 0, st>>>(coef, lv.nC, lv.N, cell_e);
-      lsqp_line_table_kernel<1><<<gl, 128, 0, st>>>(coef, cell_e, lv.nC, lv.N, table);
+      lsqp_plane64_kernel<1><<<gl, 128, 0, st>>>(coef, cell_e, lv.nC, lv.N, table);
       break;
     case 2:
       lsqp_scale_kernel<2><<<gs, 128, 0, st>>>(coef, lv.nC, lv.N, cell_e);
-      lsqp_line_table_kernel<2><<<gl, 128, 0, st>>>(coef, cell_e, lv.nC, lv.N, table);
+      lsqp_plane64_kernel<2><<<gl, 128, 0, st>>>(coef, cell_e, lv.nC, lv.N, table);
       break;
     case 3:
       lsqp_scale_kernel<3><<<gs, 128, 0, st>>>(coef, lv.nC, lv.N, cell_e);
-      lsqp_line_table_kernel<3><<<gl, 128, 0, st>>>(coef, cell_e, lv.nC, lv.N, table);
+      lsqp_plane64_kernel<3><<<gl, 128, 0, st>>>(coef, cell_e, lv.nC, lv.N, table);
       break;
     default:
       throw Error{HHG_EINVAL, "q must be 1, 2 or 3"};

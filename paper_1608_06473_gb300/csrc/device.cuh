@@ -246,4 +246,25 @@ __device__ __forceinline__ T eval_plane(const T* P, T i, T j) {
 template <int Q>
 __host__ __device__ constexpr int np_pad() { return ((Q + 1) * (Q + 2) / 2 + 3) / 4 * 4; }
 
+// Per-plane coefficients of the FP32 surrogate, paired by direction for
+// packed FP32 arithmetic: pair m holds directions 2m and 2m + 1 (the centre,
+// 14, is paired with zeros), NPP2 float2 per pair (a multiple of 16 bytes).
+template <int Q>
+__host__ __device__ constexpr int npp2() { return ((Q + 1) * (Q + 2) / 2 + 1) / 2 * 2; }
+constexpr int NPAIR = 8;
+
+// Two directions' polynomials in (i, j) at once (packed FP32 FMA).
+template <int Q>
+__device__ __forceinline__ float2 eval_plane2(const float2* P, float2 I, float2 J) {
+  float2 s = make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int a = Q; a >= 0; --a) {
+    float2 c = P[plane_index<Q>(a, Q - a)];
+#pragma unroll
+    for (int b = Q - a - 1; b >= 0; --b) c = __ffma2_rn(c, J, P[plane_index<Q>(a, b)]);
+    s = (a == Q) ? c : __ffma2_rn(s, I, c);
+  }
+  return s;
+}
+
 }  // namespace hhg

@@ -42,15 +42,30 @@ void launch_cell<float>(const LevelView<float>& lv, int op, Mode mode, float* u,
 // aligned and its plane ring fits in shared memory.  A bounded wait that
 // gives up sets *lv.err.
 constexpr int STAGE32_CONFIGS = 4;
-static_assert(STAGE32_CONFIGS <= STAGE32_CONFIGS_MAX, "tuner table too small");
 bool stage32_supported(const LevelView<float>& lv, const float* u, int cfg);
 void launch_stage32_smooth(const LevelView<float>& lv, float* u, const float* f, int cfg, cudaStream_t st);
 
-// FP64 surrogate line table (fit time): per cell the scale exponent E and,
-// per line (j, k), the q+1 coefficients of each of the 15 polynomials in i,
-// times 2^E, rounded to int64.
-void launch_line_table(const LevelView<double>& lv, int q, const double* coef, int* cell_e, long long* table,
-                       cudaStream_t st);
+// FP32 surrogate smoother as a plane wavefront per cell (wave.cu): the four
+// cell colour steps in one launch per sweep, u updated in place through the
+// caches, one barrier per step.  cfg 0, 1: 256, 512 threads per CTA.  A
+// configuration is supported when the surrogate is fitted and the cell's
+// plane table fits in shared memory.
+constexpr int WAVE32_CONFIGS = 2;
+static_assert(STAGE32_CONFIGS + WAVE32_CONFIGS == SMOOTH32_CONFIGS, "tuner table size");
+bool wave32_supported(const LevelView<float>& lv, int cfg);
+void launch_wave32_smooth(const LevelView<float>& lv, float* u, const float* f, int cfg, cudaStream_t st);
+
+// Whether smoother configuration cfg >= 0 (staged 0..3, wavefront 4..5) can run
+// on this level and vector.
+inline bool smooth32_supported(const LevelView<float>& lv, const float* u, int cfg) {
+  return cfg < STAGE32_CONFIGS ? stage32_supported(lv, u, cfg) : wave32_supported(lv, cfg - STAGE32_CONFIGS);
+}
+
+// FP64 surrogate plane table (fit time): per cell the scale exponent E and,
+// per plane k and direction, the (q+1)(q+2)/2 coefficients of the
+// polynomial in (i, j), times 2^E, rounded to int64.
+void launch_plane64_table(const LevelView<double>& lv, int q, const double* coef, int* cell_e, long long* table,
+                          cudaStream_t st);
 
 // FP32 surrogate plane table (fit time): per cell, plane k and direction the
 // (q+1)(q+2)/2 coefficients of the polynomial in (i, j), rounded to FP32.

@@ -31,6 +31,9 @@ using Clock = std::chrono::steady_clock;
 using Key = std::tuple<double, double, int, int, int>;
 
 Key key_of(const hhg_problem& p) { return Key{p.r_inner, p.r_outer, p.tang_refine, p.radial_layers, p.L}; }
+// The bytes of a built hierarchy depend on the macro mesh and level only.
+using SizeKey = std::tuple<int, int, int>;
+SizeKey size_key_of(const hhg_problem& p) { return SizeKey{p.tang_refine, p.radial_layers, p.L}; }
 
 struct Request {
   int64_t id = 0;
@@ -75,6 +78,8 @@ struct hhg_server {
   bool building = false; // one hierarchy is built at a time (it may take the whole free budget)
   int64_t next_id = 1;
   int64_t n_built = 0;
+  int64_t n_evicted = 0;
+  std::map<hhg::SizeKey, size_t> built_bytes;  // bytes of the last hierarchy built per mesh and level
   int active = 0;
   bool stop = false;
   std::vector<std::thread> workers;
@@ -163,6 +168,7 @@ void evict_for(hhg_server* s, size_t need) {
     hhg_destroy(s->cache[lru]->shell);
     s->used -= s->cache[lru]->bytes;
     s->cache.erase(s->cache.begin() + lru);
+    ++s->n_evicted;
   }
 }
 
@@ -297,7 +303,12 @@ void worker(hhg_server* s) {
         size_t budget;
         {
           std::lock_guard<std::mutex> lk(s->mu);
-          if (attempt == 1) evict_for(s, s->d.hbm_budget_bytes ? s->d.hbm_budget_bytes : 0);
+          // evict least-recently-used idle hierarchies: as many as the bytes
+          // of an earlier build of this mesh and level need, else all idle ones
+          if (attempt == 1) {
+            auto h = s->built_bytes.find(size_key_of(r->prob));
+            evict_for(s, h != s->built_bytes.end() ? h->second : s->d.hbm_budget_bytes);
+          }
           budget = s->d.hbm_budget_bytes ? s->free_budget() : 0;
         }
         if (s->d.hbm_budget_bytes && budget == 0) continue;
@@ -332,6 +343,7 @@ void worker(hhg_server* s) {
         res->shell = sh;
         res->bytes = sh->alloc.used;
         res->busy = true;
+        s->built_bytes[size_key_of(r->prob)] = res->bytes;
         s->used += res->bytes;
         s->cache.push_back(std::move(res));
         ++s->n_built;
@@ -457,7 +469,7 @@ hhg_status hhg_server_wait(hhg_server* s, int64_t ticket, double* u, double* rel
   return st;
 }
 
-hhg_status hhg_server_stats(hhg_server* s, int* n_resident, size_t* bytes, int64_t* n_built) {
+hhg_status hhg_server_stats(hhg_server* s, int* n_resident, size_t* bytes, int64_t* n_built, int64_t* n_evicted) {
   if (!s) {
     set_error("NULL server");
     return HHG_EINVAL;
@@ -468,6 +480,7 @@ hhg_status hhg_server_stats(hhg_server* s, int* n_resident, size_t* bytes, int64
   if (n_resident) *n_resident = (int)s->cache.size();
   if (bytes) *bytes = b;
   if (n_built) *n_built = s->n_built;
+  if (n_evicted) *n_evicted = s->n_evicted;
   set_error("");
   return HHG_OK;
 }

@@ -12,7 +12,9 @@
 
 namespace hhg {
 
-constexpr int STAGE32_CONFIGS_MAX = 4;  // staged FP32 smoother configurations (stage.cu)
+// FP32 surrogate smoother configurations the tuner chooses from besides the
+// per-colour node kernels: 0..3 staged (stage.cu), 4..5 wavefront (wave.cu)
+constexpr int SMOOTH32_CONFIGS = 6;
 constexpr int TUNE_NONE = -9;           // FP32 smoother of a level not tuned yet
 
 // Geometry of one macro cell: its 4 vertices (ascending global id) and the
@@ -61,11 +63,11 @@ struct LevelView {
   T* ghost;                      // [nC * n_full] per-cell copies of boundary values
   const T* coef;                 // [nC * 15 * m_q] surrogate coefficients (raw index monomials)
   int q;                         // surrogate degree (0 = not fitted)
-  // FP64 surrogate: per cell and line (j, k), the 15 polynomials in i as
-  // integers scaled by 2^cell_e[c] (records of line_rec(q) int64)
-  const long long* line64;
+  // FP64 surrogate: per cell, plane k and direction, the coefficients of
+  // the polynomial in (i, j) as integers scaled by 2^cell_e[c]
+  // ([nC][N - 3][15][npp64(q)] int64)
+  const long long* plane64;
   const int* cell_e;             // [nC]
-  int n_lines;                   // lines per cell, (N - 3)(N - 2) / 2
   const float* plane32;          // FP32 surrogate: per cell, plane and direction the polynomial in (i, j)
   const uint32_t* colour_nodes;  // interior points (packed) per colour, deep-interior ones first
   const uint32_t* all_nodes;     // all interior points, deep-interior ones first
@@ -81,7 +83,7 @@ struct LevelView {
   const int* low_pos;            // [off_C]
   const T* low_diag;             // [off_C]
   int* err;                      // device error word: set to 1 when a bounded wait gives up
-  int smooth_cfg;                // FP32 surrogate smoother: -1 / -2 = per-colour node kernel (1 / 2 nodes per thread in flight), >= 0 = staged
+  int smooth_cfg;                // FP32 surrogate smoother: -1 / -2 = per-colour node kernel (1 / 2 nodes per thread in flight), 0..3 = staged, 4..5 = wavefront
   // right-hand sides processed together: vector b of a level lives at
   // v + b vstride, its halo copy at ghost + b gstride, its residual partials
   // at partial + b pstride, its lower-step buffer at tmp + b tstride
@@ -130,7 +132,7 @@ struct Level {
   // surrogate
   double* d_coef = nullptr;
   float* d_coef32 = nullptr;
-  long long* d_line64 = nullptr;
+  long long* d_plane64 = nullptr;
   float* d_plane32 = nullptr;
   int* d_cell_e = nullptr;
   uint32_t* d_colour_nodes = nullptr;
@@ -138,9 +140,10 @@ struct Level {
   int colour_off[5] = {0, 0, 0, 0, 0};
   // FP32 surrogate smoother chosen by the tuner (TUNE_NONE = not tuned, -1 =
   // per-colour node kernel, -2 = the same with two nodes per thread in flight,
-  // >= 0 = staged configuration) and the candidates' times (ms; index cfg + 2)
+  // 0..3 = staged, 4..5 = wavefront configuration) and the candidates' times
+  // (ms; index cfg + 2)
   int tune32 = TUNE_NONE;
-  double tune32_ms[2 + STAGE32_CONFIGS_MAX] = {};
+  double tune32_ms[2 + SMOOTH32_CONFIGS] = {};
   // halo copies and work vectors (allocated on demand)
   double* d_ghost64 = nullptr;
   float* d_ghost32 = nullptr;
@@ -158,13 +161,12 @@ struct Level {
 // Number of monomials of total degree <= q in three variables (Eq. 3.2).
 HD int n_coeffs(int q) { return (q + 1) * (q + 2) * (q + 3) / 6; }
 
-// int64 per line record of the FP64 surrogate: 15 (q + 1) rounded up to a
-// multiple of 16 (128-byte aligned records).
-HD int line_rec(int q) { return (15 * (q + 1) + 15) / 16 * 16; }
-
-// Lines (j, k) of a cell's interior, k = 1..N-3, j = 1..N-2-k, in (k, j) order.
-HD int64_t n_cell_lines(int N) { return (int64_t)(N - 3) * (N - 2) / 2; }
-HD int line_id(int j, int k, int N) { return (k - 1) * (N - 2) - k * (k - 1) / 2 + (j - 1); }
+// int64 per direction in the FP64 plane table: the (q + 1)(q + 2) / 2
+// coefficients of a polynomial in (i, j), rounded up to an even count
+// (16-byte aligned records).
+HD int npp64(int q) { return ((q + 1) * (q + 2) / 2 + 1) / 2 * 2; }
+// FP64 plane table length (int64 values) for nC cells.
+HD int64_t plane64_len(int64_t nC, int N, int q) { return nC * (N - 3) * 15 * npp64(q); }
 
 }  // namespace hhg
 

@@ -24,6 +24,7 @@
 // into a small ring of shared-memory tables and evaluated per node (Sec. 3.4).
 #include <cuda_runtime.h>
 
+#include "arith.cuh"
 #include "device.cuh"
 #include "kernels.h"
 #include "ptx.cuh"
@@ -48,13 +49,6 @@ __host__ __device__ inline int plane_size(int N, int k) { return (N - 2 - k) * (
 // (the slot keeps the plane's global 16-byte phase), rounded up to 16 bytes.
 __host__ __device__ inline int slot_floats(int N) { return (plane_size(N, 1) + 3 + 3) & ~3; }
 
-// Per-plane coefficients of the FP32 surrogate, paired by direction for
-// packed FP32 arithmetic: pair m holds directions 2m and 2m + 1 (the centre,
-// 14, is paired with zeros), NPP2 float2 per pair (a multiple of 16 bytes).
-template <int Q>
-__host__ __device__ constexpr int npp2() { return ((Q + 1) * (Q + 2) / 2 + 1) / 2 * 2; }
-constexpr int NPAIR = 8;
-
 template <int Q, int SKEW>
 size_t stage_smem(int N) {
   return sizeof(float) * (size_t)Sched<SKEW>::RING * slot_floats(N) +
@@ -65,29 +59,6 @@ size_t stage_smem(int N) {
 // Resident CTAs per SM the register budget is sized for (64 registers a thread).
 template <int THREADS>
 constexpr int stage_min_blocks() { return THREADS >= 1024 ? 1 : 1024 / THREADS; }
-
-// n / d in FP32: the hardware reciprocal estimate refined by one
-// Newton-Raphson step x <- x + x (1 - d x), then the product.
-__device__ __forceinline__ float div_nr32(float n, float d) {
-  float x;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(x) : "f"(d));
-  x = fmaf(x, fmaf(-d, x, 1.0f), x);
-  return n * x;
-}
-
-// Two directions' polynomials in (i, j) at once (packed FP32 FMA).
-template <int Q>
-__device__ __forceinline__ float2 eval_plane2(const float2* P, float2 I, float2 J) {
-  float2 s = make_float2(0.0f, 0.0f);
-#pragma unroll
-  for (int a = Q; a >= 0; --a) {
-    float2 c = P[plane_index<Q>(a, Q - a)];
-#pragma unroll
-    for (int b = Q - a - 1; b >= 0; --b) c = __ffma2_rn(c, J, P[plane_index<Q>(a, b)]);
-    s = (a == Q) ? c : __ffma2_rn(s, I, c);
-  }
-  return s;
-}
 
 template <int Q, int THREADS, int SKEW>
 __global__ void __launch_bounds__(THREADS, stage_min_blocks<THREADS>()) lsqp_stage32_smooth(LevelView<float> lv,
@@ -108,7 +79,8 @@ __global__ void __launch_bounds__(THREADS, stage_min_blocks<THREADS>()) lsqp_sta
   const float* tab = lv.plane32 + (int64_t)c * np * 15 * NP;
   const float* ghost = lv.ghost + (int64_t)c * lv.n_full;
   const int n_plane = lv.n_plane;
-  bool failed = false;
+  // set by any thread whose bounded wait gave up; read by all after a barrier
+  __shared__ int s_fail;
 
   // the slot keeps the plane's 16-byte phase in the vector; planes 0 and
   // np + 1 have no interior points (their entries are never read)
@@ -117,8 +89,10 @@ __global__ void __launch_bounds__(THREADS, stage_min_blocks<THREADS>()) lsqp_sta
     pst[k] = ps;
     porg[k] = (k >= 1 && k <= np) ? ((k - 1) % RING) * S + (int)((cbase + ps) & 3) : 0;
   }
-  if (threadIdx.x == 0)
+  if (threadIdx.x == 0) {
     for (int r = 0; r < RING; ++r) mbar_init(&bar[r], 1);
+    s_fail = 0;
+  }
   __syncthreads();
   auto slot = [](int k) { return (k - 1) % RING; };
 
@@ -159,7 +133,7 @@ __global__ void __launch_bounds__(THREADS, stage_min_blocks<THREADS>()) lsqp_sta
   auto wait_plane = [&](int k) {
     if (k < 1 || k > np) return;
     // the n-th use of a slot (n = (k - 1) / RING) completes phase n
-    if (!mbar_wait(&bar[slot(k)], (uint32_t)(((k - 1) / RING) & 1))) failed = true;
+    if (!mbar_wait(&bar[slot(k)], (uint32_t)(((k - 1) / RING) & 1))) s_fail = 1;
   };
 
   // Eq. 5.1 at list entry e of plane k (all neighbours resident)
@@ -256,7 +230,11 @@ __global__ void __launch_bounds__(THREADS, stage_min_blocks<THREADS>()) lsqp_sta
   wait_plane(1);
   cp_async_wait_all();
   __syncthreads();
-  for (int s = 0; s <= np + 3 * SKEW; ++s) {
+  int s = 0;
+  for (; s <= np + 3 * SKEW; ++s) {
+    // a wait that gave up: no further copies, updates or write-back (u is
+    // left partly swept; the caller sees HHG_ETIMEOUT)
+    if (s_fail) break;
     writeback(s - 3 * SKEW);  // colour 3 done in step s - 1
     issue(s + 3);             // into the slot of plane s + 3 - RING, last read in step s - 1
     load_tab(s + 2);
@@ -275,7 +253,17 @@ __global__ void __launch_bounds__(THREADS, stage_min_blocks<THREADS>()) lsqp_sta
       __syncthreads();
     }
   }
-  if (failed) atomicExch(err, 1);
+  if (s_fail) {
+    // let the copies already issued land before the CTA exits (planes up to
+    // s + 2 were issued, the last two possibly not yet waited for), each
+    // wait bounded again
+    cp_async_wait_all();
+    if (threadIdx.x == 0) {
+      for (int k = s + 1; k <= s + 2; ++k)
+        if (k >= 1 && k <= np) mbar_wait(&bar[slot(k)], (uint32_t)(((k - 1) / RING) & 1));
+      atomicExch(err, 1);
+    }
+  }
 }
 
 template <int Q, int THREADS, int SKEW>

@@ -6,10 +6,13 @@ against the FP64 solve.
 FP32 bound: every weight and every update is formed from O(15) FP32 terms
 whose magnitudes exceed the result by the row's cancellation factor (about
 4 for random u), so the relative 2-norm error stays within a few hundred
-FP32 ulps; the bar used is 2e-5 (= 168 eps_32) relative."""
+FP32 ulps; the bar used is 2e-5 (= 168 eps_32) relative.  Every node must
+also meet the per-node bound of gpu_checks (C = 64 for apply, residual and
+one sweep, 128 for two sweeps), so no wrong node hides in the norm."""
 import numpy as np
 import pytest
 
+import gpu_checks as G
 import synthetic
 from oracle import fem as F
 from oracle import lsqp as LS
@@ -58,8 +61,13 @@ def test_f32_apply_residual(c1, opname):
     op = ops[opname]
     yr = op.apply(u.astype(np.float64))
     rr = op.residual(u.astype(np.float64), f.astype(np.float64))
-    assert rel(y.cpu().numpy().astype(np.float64), yr, lv.free) <= TOL32
-    assert rel(r.cpu().numpy().astype(np.float64), rr, lv.free) <= TOL32
+    yg, rg = y.cpu().numpy().astype(np.float64), r.cpu().numpy().astype(np.float64)
+    assert rel(yg, yr, lv.free) <= TOL32
+    assert rel(rg, rr, lv.free) <= TOL32
+    absAu = abs(op.A) @ np.abs(op.mask * u.astype(np.float64))
+    fr = lv.free
+    G.assert_per_node(yg[fr], yr[fr], absAu[fr], 64, "apply")
+    G.assert_per_node(rg[fr], rr[fr], absAu[fr] + np.abs(f[fr].astype(np.float64)), 64, "residual")
     assert abs(nrm - np.linalg.norm(rr)) <= TOL32 * np.linalg.norm(rr)
 
 
@@ -75,7 +83,11 @@ def test_f32_smoother(c1, opname):
     ref = op.mask * u.astype(np.float64)
     for _ in range(2):
         ref = op.sweep(ref, f.astype(np.float64))
-    assert rel(ut.cpu().numpy().astype(np.float64), ref, lv.free) <= TOL32
+    got = ut.cpu().numpy().astype(np.float64)
+    assert rel(got, ref, lv.free) <= TOL32
+    fr = lv.free
+    scale = (abs(op.off) @ np.abs(ref) + np.abs(f.astype(np.float64)))[fr] / np.abs(op.diag[fr])
+    G.assert_per_node(got[fr], ref[fr], scale, 128, "two sweeps")
 
 
 @pytest.mark.parametrize("opname", ["ifem", "lsqp"])

@@ -98,3 +98,32 @@ def test_continuous_batching_equals_alone(dtype, tol):
         if dtype == hhg.HHG_F64:
             assert im["cycles"] == ia["cycles"]
         assert rel(um, ua) <= tol
+
+
+def test_budget_evicts_least_recently_used():
+    """Under an HBM budget that holds two hierarchies of a level but not
+    three, a request of a third key evicts the least recently used idle
+    hierarchy (one, not all), and a later request of the evicted key
+    rebuilds it; results equal those of an unbudgeted server (FP64: the same
+    arithmetic on a rebuilt hierarchy)."""
+    keys = [(0.45, 4), (0.55, 4), (0.65, 4), (0.45, 4)]
+    fs = [rhs(300 + k, ri, L, 1) for k, (ri, L) in enumerate(keys)]
+    with hhg.Server(max_inflight=1, dtype=hhg.HHG_F64) as srv:
+        ref = [srv.wait(srv.submit(f, r_inner=ri, L=L)) for f, (ri, L) in zip(fs, keys)]
+        st0 = srv.stats()
+    assert st0["built"] == 3 and st0["evicted"] == 0
+    per = st0["bytes"] / 3
+    vec = 2 * fs[0].size * 8
+    # room for two resident hierarchies and a few request vectors, not for a third
+    with hhg.Server(hbm_budget_bytes=int(2 * per) + 4 * vec, max_inflight=1, dtype=hhg.HHG_F64) as srv:
+        got = []
+        for f, (ri, L) in zip(fs, keys):
+            got.append(srv.wait(srv.submit(f, r_inner=ri, L=L)))
+            assert srv.stats()["resident"] <= 2
+        st = srv.stats()
+    # key 0 evicted by key 2, then key 1 by the rebuild of key 0
+    assert st["evicted"] == 2 and st["built"] == 4
+    assert [i["reused"] for _, _, i in got] == [0, 0, 0, 0]
+    for (ug, rg, _), (ur, rr, _) in zip(got, ref):
+        assert np.all(rg <= 1e-8)
+        assert rel(ug, ur) <= 1e-12

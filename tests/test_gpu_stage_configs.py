@@ -1,14 +1,17 @@
 """Every launch configuration of the FP32 surrogate smoother (the
 per-colour thread-per-node kernel with one or two nodes per thread in
-flight, and the shared-memory staged one-launch
-kernel at wavefront skew 1 and 2 with its CTA sizes) against the FP64
+flight, the shared-memory staged one-launch kernel at wavefront skew 1 and
+2 with its CTA sizes, and the plane-wavefront one-launch kernel with 256 and
+512 threads) against the FP64
 oracle, on the 60-macro shell at N = 16 (whole vector) and N = 32 / 64
-(sampled cells, the FP32 bound of test_gpu_f32: 2e-5 relative), pinned
+(sampled cells, the FP32 bound of test_gpu_f32: 2e-5 relative, and the
+per-node bound of gpu_checks: C = 128 for two sweeps, 64 for one), pinned
 through hhg_set_tuning; and the tuner's choice is a configuration that
 fits."""
 import numpy as np
 import pytest
 
+import gpu_checks as G
 import synthetic
 from oracle import fem as F
 from oracle import local as LO
@@ -22,7 +25,7 @@ pytestmark = pytest.mark.gpu
 import paper_1608_06473_gb300 as hhg  # noqa: E402
 
 TOL32 = 2e-5
-CONFIGS = [-2, -1, 0, 1, 2, 3]
+CONFIGS = [-2, -1, 0, 1, 2, 3, 4, 5]
 
 
 def rel(a, b):
@@ -53,10 +56,14 @@ def test_configs_whole_vector_n16(c1, cfg):
     ref = op.mask * u.astype(np.float64)
     for _ in range(2):
         ref = op.sweep(ref, f.astype(np.float64))
-    assert rel(ut.cpu().numpy().astype(np.float64)[lv.free], ref[lv.free]) <= TOL32
+    got = ut.cpu().numpy().astype(np.float64)
+    fr = lv.free
+    assert rel(got[fr], ref[fr]) <= TOL32
+    scale = (abs(op.off) @ np.abs(ref) + np.abs(f.astype(np.float64)))[fr] / np.abs(op.diag[fr])
+    G.assert_per_node(got[fr], ref[fr], scale, 128, f"config {cfg}")
 
 
-@pytest.mark.parametrize("L", [5, 6])
+@pytest.mark.parametrize("L", [5, 6, 7])
 def test_configs_sampled_cells(L):
     N = 2 ** L
     sh = M.make_shell()
@@ -83,6 +90,8 @@ def test_configs_sampled_cells(L):
                 lr, lc = np.searchsorted(idx, rows), np.searchsorted(idx, cols)
                 got = LO.interior_colour_steps(lr, lc, W, col, start.copy(), f[idx].astype(np.float64))
                 assert rel(ua[rows], got[lr]) <= TOL32, (cfg, c)
+                scale = G.cell_smoother_scale(W, lc, got, f[rows].astype(np.float64))
+                G.assert_per_node(ua[rows], got[lr], scale, 64, f"config {cfg} cell {c}")
         # the configurations differ only in rounding order
         for cfg in CONFIGS:
             assert rel(outs[cfg], outs[-1]) <= TOL32
