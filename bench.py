@@ -92,7 +92,8 @@ def parse():
     p.add_argument("--j", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--mode", choices=["solve", "smoother", "serve", "variants", "discretisation", "batch", "peaks"],
+    p.add_argument("--mode", choices=["solve", "smoother", "serve", "variants", "discretisation", "batch", "peaks",
+                                      "traffic"],
                    default="solve",
                    help="solve: the whole path per step (default); smoother: finest-level sweeps only "
                         "(for profiling the smoother kernels)")
@@ -117,6 +118,15 @@ def parse():
     p.add_argument("--no-mixed-c3", action="store_true",
                    help="skip the mixed-precision vs FP64 solve on the N=128 shell reported beside the default line")
     p.add_argument("--batch-rhs", type=int, default=32, help="--mode batch: right-hand sides of the batched solve")
+    p.add_argument("--ncu-report", type=str, default=None,
+                   help="--mode traffic: ncu report (.ncu-rep) holding DRAM counters of one launch of the kernel")
+    p.add_argument("--traffic-key", type=str, default="lsqp_node_smooth_f64",
+                   help="--mode traffic: record key (kernel) in profiles/traffic.txt")
+    p.add_argument("--traffic-source", type=str, default="cell.cu",
+                   help="--mode traffic: source file of the kernel (its hash gates the record)")
+    p.add_argument("--traffic-scale", type=float, default=8.0,
+                   help="--mode traffic: captured launch -> one sweep of the bench workload (launches per sweep x "
+                        "units ratio)")
     return p.parse_args()
 
 
@@ -365,10 +375,7 @@ def run_ours(args, rank, world, local):
     else:
         achieved = 12 * units_per_sweep / sweep_s / 1e9
         cfg = hhg.hhg_tuning(s.handle, L)[0]
-        kname = ("lsqp_stage32_smooth<%d> (finest level, one launch per sweep, planes staged in shared memory; "
-                 "tuned configuration %d)" % (args.q, cfg)) if cfg >= 0 else \
-            ("lsqp_node32_%skernel<%d,SMOOTH> (finest level, tuned: one launch per colour)"
-             % ("x2_" if cfg == -2 else "", args.q))
+        kname = smoother32_name(cfg, args.q)
         roofline = {"kernel": kname,
                     "bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s",
                     "frac": achieved / hbm_gbs,
@@ -403,6 +410,17 @@ def run_ours(args, rank, world, local):
         out["speedup_over_f64_solve"] = mp["speedup_over_f64_solve"]
         out["speedup_over_f64_solve_workload"] = mp["workload"]
     return out
+
+
+def smoother32_name(cfg, q):
+    """The FP32 cell smoother kernel of tuner configuration cfg."""
+    if cfg >= 4:
+        return ("lsqp_wave32_smooth<%d,%d> (finest level, one launch per sweep: plane wavefront per cell, u in place "
+                "through L1/L2)" % (q, 256 if cfg == 4 else 512))
+    if cfg >= 0:
+        return ("lsqp_stage32_smooth<%d> (finest level, one launch per sweep, planes staged in shared memory; "
+                "configuration %d)" % (q, cfg))
+    return "lsqp_node32_%skernel<%d,SMOOTH> (finest level, one launch per colour)" % ("x2_" if cfg == -2 else "", q)
 
 
 def mixed_vs_f64(workload, q, j):
@@ -455,7 +473,8 @@ def mixed_vs_f64(workload, q, j):
     hbm_gbs, hbm_note = hbm_peak()
     sweep = out["mixed"]["cell_sweep_ms"] * 1e-3
     cfg = hhg.hhg_tuning(s.handle, L)[0]
-    out["fp32_smoother"] = {"tuned_cfg": cfg, "cell_sweep_ms": sweep * 1e3, "glups": units / sweep / 1e9,
+    out["fp32_smoother"] = {"tuned_cfg": cfg, "kernel": smoother32_name(cfg, q), "cell_sweep_ms": sweep * 1e3,
+                            "glups": units / sweep / 1e9,
                             "algorithmic_gbs": 12 * units / sweep / 1e9, "hbm_frac": 12 * units / sweep / 1e9 / hbm_gbs,
                             "peak_note": hbm_note}
     out["f64_smoother"] = {"cell_sweep_ms": out["f64"]["cell_sweep_ms"],
@@ -873,6 +892,35 @@ def run_batch(args):
     return out
 
 
+def run_traffic(args):
+    """Writes the DRAM traffic record the bench's roofline reads
+    (profiles/traffic.txt): dram__bytes_read.sum + dram__bytes_write.sum of
+    the first launch in an ncu report, times --traffic-scale (launches per
+    sweep x the bench workload's units over the captured launch's), keyed by
+    kernel and workload and gated by the hash of the kernel's source file."""
+    import csv
+    import io
+    res = subprocess.run(["ncu", "-i", args.ncu_report, "--page", "raw", "--csv"], capture_output=True, text=True,
+                         check=True)
+    rows = list(csv.reader(io.StringIO(res.stdout)))
+    hdr, units, first = rows[0], rows[1], rows[2]
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
+    val = lambda name: float(first[hdr.index(name)]) * scale[units[hdr.index(name)]]
+    per_launch = val("dram__bytes_read.sum") + val("dram__bytes_write.sum")
+    src = open(os.path.join(ROOT, "paper_1608_06473_gb300", "csrc", args.traffic_source), "rb").read()
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    recs = json.load(open(path)) if os.path.exists(path) else {}
+    key = f"{args.traffic_key}@{args.workload}"
+    recs[key] = {"source": args.traffic_source, "sha256_16": hashlib.sha256(src).hexdigest()[:16],
+                 "dram_bytes_per_sweep": per_launch * args.traffic_scale,
+                 "captured_launch_bytes": per_launch, "scale": args.traffic_scale,
+                 "kernel": first[hdr.index("Kernel Name")] if "Kernel Name" in hdr else None,
+                 "note": "written by bench.py --mode traffic from %s" % os.path.basename(args.ncu_report)}
+    with open(path, "w") as fh:
+        json.dump(recs, fh, indent=1)
+    return {"mode": "traffic", "key": key, **recs[key]}
+
+
 def run_peaks(args):
     import torch
 
@@ -941,6 +989,9 @@ def main():
         return
     if args.mode == "peaks":
         print(json.dumps(run_peaks(args)))
+        return
+    if args.mode == "traffic":
+        print(json.dumps(run_traffic(args)))
         return
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))
