@@ -118,6 +118,7 @@ def parse():
     p.add_argument("--no-mixed-c3", action="store_true",
                    help="skip the mixed-precision vs FP64 solve on the N=128 shell reported beside the default line")
     p.add_argument("--batch-rhs", type=int, default=32, help="--mode batch: right-hand sides of the batched solve")
+    p.add_argument("--nrhs", type=int, default=1, help="--mode smoother: right-hand sides smoothed together")
     p.add_argument("--ncu-report", type=str, default=None,
                    help="--mode traffic: ncu report (.ncu-rep) holding DRAM counters of one launch of the kernel")
     p.add_argument("--traffic-key", type=str, default="lsqp_node_smooth_f64",
@@ -414,9 +415,12 @@ def run_ours(args, rank, world, local):
 
 def smoother32_name(cfg, q):
     """The FP32 cell smoother kernel of tuner configuration cfg."""
+    if cfg >= 6:
+        return ("lsqp_chunk32_smooth<%d> (finest level, one launch per colour; a thread takes up to 4 points of a "
+                "line)" % q)
     if cfg >= 4:
         return ("lsqp_wave32_smooth<%d,%d> (finest level, one launch per sweep: plane wavefront per cell, u in place "
-                "through L1/L2)" % (q, 256 if cfg == 4 else 512))
+                "through L1/L2)" % (q, 128 if cfg == 4 else 256))
     if cfg >= 0:
         return ("lsqp_stage32_smooth<%d> (finest level, one launch per sweep, planes staged in shared memory; "
                 "configuration %d)" % (q, cfg))
@@ -935,7 +939,8 @@ def run_peaks(args):
 
 def run_smoother(args):
     """Finest-level smoother only: setup, fit, `warmup` sweeps, then `steps`
-    sweeps timed with CUDA events on the launching stream."""
+    sweeps timed with CUDA events on the launching stream, over --nrhs
+    right-hand sides at once (u ~ U[-1, 1] seed 1 + b, f ~ U[-1, 1] seed b)."""
     import torch
 
     import paper_1608_06473_gb300 as hhg
@@ -949,16 +954,19 @@ def run_smoother(args):
         s.fit(args.q, args.j, stream=stream)
     dt = torch.float32 if args.precision == "mixed" else torch.float64
     dtype = hhg.HHG_F32 if args.precision == "mixed" else hhg.HHG_F64
-    f = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_F)).cuda().to(dt)
-    u = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_U)).cuda().to(dt)
+    nb = args.nrhs
+    f = torch.from_numpy(np.stack([synthetic.uniform(n_total, synthetic.SEED_F + b) for b in range(nb)])).cuda().to(dt)
+    u = torch.from_numpy(np.stack([synthetic.uniform(n_total, synthetic.SEED_U + b) for b in range(nb)])).cuda().to(dt)
+    if nb == 1:
+        f, u = f[0].contiguous(), u[0].contiguous()
     if args.smooth_cfg is not None and args.precision == "mixed":
-        s.smooth(f, u.clone(), 1, op=opcode, dtype=dtype, stream=stream)   # allocates and tunes the FP32 buffers
+        s.smooth(f, u.clone(), 1, op=opcode, dtype=dtype, nrhs=nb, stream=stream)   # allocates and tunes FP32
         hhg.hhg_set_tuning(s.handle, L, args.smooth_cfg)
-    s.smooth(f, u, args.warmup, op=opcode, dtype=dtype, stream=stream)
+    s.smooth(f, u, args.warmup, op=opcode, dtype=dtype, nrhs=nb, stream=stream)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    s.smooth(f, u, args.steps, op=opcode, dtype=dtype, stream=stream)
+    s.smooth(f, u, args.steps, op=opcode, dtype=dtype, nrhs=nb, stream=stream)
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
@@ -966,8 +974,8 @@ def run_smoother(args):
     s.close()
     return {"mode": "smoother", "op": args.op, "precision": "f32" if args.precision == "mixed" else "f64",
             "tuning": None if tuning is None else {"cfg": tuning[0], "ms": list(tuning[1])},
-            "workload": args.workload, "sweeps": args.steps,
-            "ms_per_sweep": ms / args.steps, "GLUP/s": n_free * args.steps / (ms * 1e-3) / 1e9}
+            "workload": args.workload, "sweeps": args.steps, "nrhs": nb,
+            "ms_per_sweep": ms / args.steps, "GLUP/s": nb * n_free * args.steps / (ms * 1e-3) / 1e9}
 
 
 def main():

@@ -382,8 +382,9 @@ hhg_status hhg_timing_read(hhg_shell* shell, int which, double* total_ms, int64_
  * flight, 0..3 for the shared-memory staged one-launch kernel with
  * (wavefront skew, threads per CTA) = (1, 256), (1, 1024), (2, 128),
  * (2, 512), 4..5 for the plane-wavefront one-launch kernel (u in place
- * through the caches) with 256 and 512 threads per CTA; -9 if not tuned.
- * ms (nullable, 8 entries) receives each candidate's best time for one cell
+ * through the caches) with 128 and 256 threads per CTA, 6 for the
+ * per-colour kernel over chunks of up to 4 points of a line; -9 if not
+ * tuned.  ms (nullable, 9 entries) receives each candidate's best time for one cell
  * sweep, candidate cfg at ms[cfg + 2] (-1 = not run).  The FP32 apply and
  * residual use the two-nodes variant when the smoother does.  Batched calls
  * (nrhs > 1) smooth with the per-colour kernel that forms every node's
@@ -391,7 +392,8 @@ hhg_status hhg_timing_read(hhg_shell* shell, int which, double* total_ms, int64_
 hhg_status hhg_tuning(const hhg_shell* shell, int L, int* cfg, double* ms);
 
 /* Pins the FP32 surrogate smoother of level L to configuration cfg (-2, -1,
- * a staged configuration 0..3 or a wavefront configuration 4..5 as above)
+ * a staged configuration 0..3, a wavefront configuration 4..5 or the
+ * chunked configuration 6 as above)
  * until the next fit; a one-launch configuration that does not fit the
  * level falls back to the per-colour kernel at launch.  HHG_EINVAL for an
  * unknown cfg. */

@@ -175,7 +175,7 @@ def hhg_check_arith(which: int, a, b, out, n: int, stream=None):
 def hhg_tuning(shell: int, L: int):
     """(chosen FP32 smoother configuration, per-candidate ms) of level L."""
     cfg = ctypes.c_int()
-    ms = np.zeros(8)
+    ms = np.zeros(9)
     _check(lib().hhg_tuning(shell, L, ctypes.byref(cfg), ms.ctypes.data))
     return cfg.value, ms
 

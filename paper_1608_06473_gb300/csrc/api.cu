@@ -248,6 +248,28 @@ static void build_level(hhg_shell* s, int n, cudaStream_t st) {
       for (int j = 1; j < N - k; ++j)
         for (int i = 1; i < N - j - k; ++i)
           if (deep(i, j, k) == (pass == 0)) all_nodes.push_back(pack_ijk(i, j, k));
+  // chunked colour lists: up to CHUNK32 deep points of a line (stride 4),
+  // then the points of the colour next to the cell boundary
+  std::vector<uint32_t> chunk_nodes;
+  for (int cc = 0; cc < 4; ++cc) {
+    L.chunk_off[cc] = (int)chunk_nodes.size();
+    for (int k = 2; k < N; ++k)
+      for (int j = 2; j < N - k; ++j) {
+        const int last = N - 2 - j - k;
+        int i = 2;
+        while ((i + 2 * j + 3 * k) % 4 != cc) ++i;
+        for (; i <= last; i += 4 * CHUNK32) {
+          const int cnt = std::min(CHUNK32, (last - i) / 4 + 1);
+          chunk_nodes.push_back(pack_ijk(i, j, k) | ((uint32_t)(cnt - 1) << 30));
+        }
+      }
+    L.chunk_mid[cc] = (int)chunk_nodes.size();
+    for (int k = 1; k < N; ++k)
+      for (int j = 1; j < N - k; ++j)
+        for (int i = 1; i < N - j - k; ++i)
+          if (!deep(i, j, k) && (i + 2 * j + 3 * k) % 4 == cc) chunk_nodes.push_back(pack_ijk(i, j, k));
+  }
+  L.chunk_off[4] = (int)chunk_nodes.size();
   std::vector<uint32_t> bnd_ijk;
   std::vector<int> bnd_slot;
   boundary_points(N, bnd_ijk, bnd_slot);
@@ -301,6 +323,7 @@ static void build_level(hhg_shell* s, int n, cudaStream_t st) {
   L.d_int_ijk = upload(A, int_ijk, st);
   L.d_colour_nodes = upload(A, colour_nodes, st);
   L.d_all_nodes = upload(A, all_nodes, st);
+  L.d_chunk_nodes = upload(A, chunk_nodes, st);
   L.d_bnd_ijk = upload(A, bnd_ijk, st);
   L.d_bnd_slot = upload(A, bnd_slot, st);
   L.d_halo_src = upload(A, halo_src, st);
@@ -438,6 +461,9 @@ LevelView<float> view<float>(hhg_shell* s, int n) {
   v.colour_nodes = d.colour_nodes;
   v.all_nodes = d.all_nodes;
   for (int cc = 0; cc < 5; ++cc) v.colour_off[cc] = d.colour_off[cc];
+  v.chunk_nodes = L.d_chunk_nodes;
+  for (int cc = 0; cc < 5; ++cc) v.chunk_off[cc] = L.chunk_off[cc];
+  for (int cc = 0; cc < 4; ++cc) v.chunk_mid[cc] = L.chunk_mid[cc];
   v.sell_ptr = d.sell_ptr; v.sell_col = d.sell_col; v.sell_val = L.d_sell_val32; v.low_diag = L.d_low_diag32;
   v.low_perm = d.low_perm; v.low_pos = d.low_pos;
   v.err = d.err;

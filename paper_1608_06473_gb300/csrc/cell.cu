@@ -498,6 +498,96 @@ __global__ void __launch_bounds__(NODE_THREADS, 4) lsqp_node32_x2_kernel(LevelVi
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 surrogate smoother over chunked colour lists: a thread takes up to
+// CHUNK32 deep-interior points i0, i0 + 4, .. of one line (j, k) of the
+// colour, so the index arithmetic (position, the 14 neighbour offsets of the
+// line) and each direction pair's line coefficients C_a(j) are formed once
+// per chunk; per point the weights are a Horner step in i (packed FP32 FMA).
+// The same operations in the same order as eval_plane2, so the same FP32
+// weights as the one-point kernels.  Points next to the cell boundary are
+// single items.  blockIdx.x = (cell - c0) * splits + part: a cell's items are
+// shared by `splits` CTAs.
+// ---------------------------------------------------------------------------
+template <int Q>
+__global__ void __launch_bounds__(NODE_THREADS, 4) lsqp_chunk32_smooth(LevelView<float> lv,
+                                                                      const uint32_t* __restrict__ items,
+                                                                      int n_deep, int n, int c0, int splits,
+                                                                      float* u, const float* f) {
+  constexpr int NP = (Q + 1) * (Q + 2) / 2;
+  constexpr int NP2 = npp2<Q>();
+  extern __shared__ __align__(16) float2 s_tab2[];   // [N - 3][NPAIR][NP2]
+  const int N = lv.N, np = N - 3;
+  const int c = c0 + blockIdx.x / splits, part = blockIdx.x % splits;
+  {
+    const float* tab = lv.plane32 + (int64_t)c * np * 15 * NP;
+    float* d = reinterpret_cast<float*>(s_tab2);
+    for (int t = threadIdx.x; t < np * NPAIR * NP2 * 2; t += blockDim.x) {
+      const int h = t & 1, e = (t >> 1) % NP2, m = ((t >> 1) / NP2) % NPAIR, k = (t >> 1) / (NP2 * NPAIR);
+      const int w = 2 * m + h;
+      d[t] = (e < NP && w < 15) ? tab[((int64_t)k * 15 + w) * NP + e] : 0.0f;
+    }
+  }
+  __syncthreads();
+  float* uc = u + lv.off_C + (int64_t)c * lv.n_int;
+  const float* fc = f + lv.off_C + (int64_t)c * lv.n_int;
+  const int t0 = (int)((int64_t)n * part / splits), t1 = (int)((int64_t)n * (part + 1) / splits);
+  for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+    const uint32_t p = items[t];
+    const int i0 = (int)(p & 1023u), j = (int)((p >> 10) & 1023u), k = (int)((p >> 20) & 1023u);
+    const float2* P = s_tab2 + (k - 1) * NPAIR * NP2;
+    const float2 Jv = make_float2((float)j, (float)j);
+    const int lin0 = lin_interior32(i0, j, k, N);
+    if (t < n_deep) {
+      const int cnt = (int)(p >> 30) + 1;
+      int off[14];
+      neighbour_offsets(j, k, N, off);
+      float2 acc[CHUNK32];
+#pragma unroll
+      for (int q = 0; q < CHUNK32; ++q) acc[q] = make_float2(0.0f, 0.0f);
+      float2 C[Q + 1];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+#pragma unroll
+        for (int a = 0; a <= Q; ++a) {
+          float2 ca = P[m * NP2 + plane_index<Q>(a, Q - a)];
+#pragma unroll
+          for (int b = Q - a - 1; b >= 0; --b) ca = __ffma2_rn(ca, Jv, P[m * NP2 + plane_index<Q>(a, b)]);
+          C[a] = ca;
+        }
+#pragma unroll
+        for (int q = 0; q < CHUNK32; ++q) {
+          if (q < cnt) {
+            const float fi = (float)(i0 + 4 * q);
+            const float2 Iv = make_float2(fi, fi);
+            float2 w2 = C[Q];
+#pragma unroll
+            for (int a = Q - 1; a >= 0; --a) w2 = __ffma2_rn(w2, Iv, C[a]);
+            if (m < 7) {
+              const int x = lin0 + 4 * q;
+              acc[q] = __ffma2_rn(w2, make_float2(uc[x + off[2 * m]], uc[x + off[2 * m + 1]]), acc[q]);
+            } else {
+              const int x = lin0 + 4 * q;
+              uc[x] = div_nr32(fc[x] - acc[q].x - acc[q].y, w2.x);
+            }
+          }
+        }
+      }
+    } else {
+      const float2 Iv = make_float2((float)i0, (float)i0);
+      float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int m = 0; m < 7; ++m) {
+        const float a = load_pt(lv, (const float*)u, c, i0 + DI(2 * m), j + DJ(2 * m), k + DK(2 * m));
+        const float b = load_pt(lv, (const float*)u, c, i0 + DI(2 * m + 1), j + DJ(2 * m + 1), k + DK(2 * m + 1));
+        acc = __ffma2_rn(eval_plane2<Q>(P + m * NP2, Iv, Jv), make_float2(a, b), acc);
+      }
+      const float wc = eval_plane2<Q>(P + 7 * NP2, Iv, Jv).x;
+      uc[lin0] = div_nr32(fc[lin0] - acc.x - acc.y, wc);
+    }
+  }
+}
+
 // FP32 surrogate for all lv.nrhs right-hand sides at once, persistent over
 // cells: per cell the per-plane table is staged once, per node the 15
 // weights (5 FMA each from the table) and the centre reciprocal are formed
@@ -685,6 +775,28 @@ void launch_node32(const LevelView<float>& lv, const uint32_t* list, int n, floa
   launch_batch<float, MODE>(lsqp_node32_batch_kernel<Q, MODE>, lv, smem, list, n, u, out, f, partial, st);
 }
 
+// The chunked FP32 smoother over one colour for cells [c0, c0 + nc), each
+// cell's items shared by `splits` CTAs.
+template <int Q>
+void launch_chunk32(const LevelView<float>& lv, int cc, int c0, int nc, int splits, float* u, const float* f,
+                    cudaStream_t st) {
+  const size_t smem = sizeof(float2) * (size_t)(lv.N - 3) * NPAIR * npp2<Q>();
+  auto kern = lsqp_chunk32_smooth<Q>;
+  ensure_smem_limit((const void*)kern, smem);
+  const int beg = lv.chunk_off[cc];
+  kern<<<nc * splits, NODE_THREADS, smem, st>>>(lv, lv.chunk_nodes + beg, lv.chunk_mid[cc] - beg,
+                                                lv.chunk_off[cc + 1] - beg, c0, splits, u, f);
+  HHG_CUDA(cudaGetLastError());
+  count_launch();
+}
+
+// One sweep of the four colours by the chunked kernel, each colour one
+// launch over all cells.
+template <int Q>
+void chunk32_sweep(const LevelView<float>& lv, float* u, const float* f, cudaStream_t st) {
+  for (int cc = 0; cc < 4; ++cc) launch_chunk32<Q>(lv, cc, 0, lv.nC, 1, u, f, st);
+}
+
 template <int Q>
 void lsqp32(const LevelView<float>& lv, Mode mode, float* u, float* out, const float* f, double* partial,
             cudaStream_t st) {
@@ -770,6 +882,19 @@ __global__ void fit_coef_kernel(int nC, int mq, int n_pts, const double* __restr
 
 }  // namespace
 
+bool chunk32_supported(const LevelView<float>& lv) {
+  if (lv.q < 1 || lv.q > 3 || lv.N < 8 || lv.plane32 == nullptr || lv.chunk_nodes == nullptr) return false;
+  static int optin = 0;
+  if (optin == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      return false;
+  }
+  const int np2 = lv.q == 1 ? npp2<1>() : (lv.q == 2 ? npp2<2>() : npp2<3>());
+  return sizeof(float2) * (size_t)(lv.N - 3) * NPAIR * np2 <= (size_t)optin;
+}
+
 template <>
 void launch_cell<double>(const LevelView<double>& lv, int op, Mode mode, double* u, double* out, const double* f,
                          double* partial, cudaStream_t st) {
@@ -794,8 +919,18 @@ void launch_cell<float>(const LevelView<float>& lv, int op, Mode mode, float* u,
     // the staged sweep holds one vector's planes; batches take the batched
     // per-colour kernel, which forms every node's weights once for all of them
     if (mode == SMOOTH && lv.nrhs == 1 && lv.smooth_cfg >= 0 && smooth32_supported(lv, u, lv.smooth_cfg)) {
-      if (lv.smooth_cfg < STAGE32_CONFIGS) launch_stage32_smooth(lv, u, f, lv.smooth_cfg, st);
-      else launch_wave32_smooth(lv, u, f, lv.smooth_cfg - STAGE32_CONFIGS, st);
+      const int cfg = lv.smooth_cfg;
+      if (cfg < STAGE32_CONFIGS) {
+        launch_stage32_smooth(lv, u, f, cfg, st);
+      } else if (cfg < STAGE32_CONFIGS + WAVE32_CONFIGS) {
+        launch_wave32_smooth(lv, u, f, cfg - STAGE32_CONFIGS, st);
+      } else {
+        switch (lv.q) {
+          case 1: chunk32_sweep<1>(lv, u, f, st); break;
+          case 2: chunk32_sweep<2>(lv, u, f, st); break;
+          default: chunk32_sweep<3>(lv, u, f, st); break;
+        }
+      }
       return;
     }
     switch (lv.q) {

@@ -47,18 +47,25 @@ void launch_stage32_smooth(const LevelView<float>& lv, float* u, const float* f,
 
 // FP32 surrogate smoother as a plane wavefront per cell (wave.cu): the four
 // cell colour steps in one launch per sweep, u updated in place through the
-// caches, one barrier per step.  cfg 0, 1: 256, 512 threads per CTA.  A
+// caches, one barrier per step.  cfg 0, 1: 128, 256 threads per CTA.  A
 // configuration is supported when the surrogate is fitted and the cell's
 // plane table fits in shared memory.
 constexpr int WAVE32_CONFIGS = 2;
-static_assert(STAGE32_CONFIGS + WAVE32_CONFIGS == SMOOTH32_CONFIGS, "tuner table size");
 bool wave32_supported(const LevelView<float>& lv, int cfg);
 void launch_wave32_smooth(const LevelView<float>& lv, float* u, const float* f, int cfg, cudaStream_t st);
 
-// Whether smoother configuration cfg >= 0 (staged 0..3, wavefront 4..5) can run
-// on this level and vector.
+// Chunked per-colour FP32 smoother (cell.cu): configuration 6, each colour
+// one launch over all cells.
+constexpr int CHUNK32_CONFIGS = 1;
+bool chunk32_supported(const LevelView<float>& lv);
+static_assert(STAGE32_CONFIGS + WAVE32_CONFIGS + CHUNK32_CONFIGS == SMOOTH32_CONFIGS, "tuner table size");
+
+// Whether smoother configuration cfg >= 0 (staged 0..3, wavefront 4..5,
+// chunked 6) can run on this level and vector.
 inline bool smooth32_supported(const LevelView<float>& lv, const float* u, int cfg) {
-  return cfg < STAGE32_CONFIGS ? stage32_supported(lv, u, cfg) : wave32_supported(lv, cfg - STAGE32_CONFIGS);
+  if (cfg < STAGE32_CONFIGS) return stage32_supported(lv, u, cfg);
+  if (cfg < STAGE32_CONFIGS + WAVE32_CONFIGS) return wave32_supported(lv, cfg - STAGE32_CONFIGS);
+  return chunk32_supported(lv);
 }
 
 // FP64 surrogate plane table (fit time): per cell the scale exponent E and,

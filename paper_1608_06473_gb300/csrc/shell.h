@@ -13,8 +13,9 @@
 namespace hhg {
 
 // FP32 surrogate smoother configurations the tuner chooses from besides the
-// per-colour node kernels: 0..3 staged (stage.cu), 4..5 wavefront (wave.cu)
-constexpr int SMOOTH32_CONFIGS = 6;
+// per-colour node kernels: 0..3 staged (stage.cu), 4..5 wavefront (wave.cu),
+// 6 chunked per-colour (cell.cu)
+constexpr int SMOOTH32_CONFIGS = 7;
 constexpr int TUNE_NONE = -9;           // FP32 smoother of a level not tuned yet
 
 // Geometry of one macro cell: its 4 vertices (ascending global id) and the
@@ -36,6 +37,9 @@ struct Allocator {
   template <class T>
   T* alloc_n(size_t n) { return static_cast<T*>(alloc(n * sizeof(T))); }
 };
+
+// Deep-interior points per chunked work item of the FP32 smoother.
+constexpr int CHUNK32 = 4;
 
 // Packed cell-local point: i | j << 10 | k << 20 (N <= 1023).
 HD uint32_t pack_ijk(int i, int j, int k) { return (uint32_t)i | ((uint32_t)j << 10) | ((uint32_t)k << 20); }
@@ -72,6 +76,13 @@ struct LevelView {
   const uint32_t* colour_nodes;  // interior points (packed) per colour, deep-interior ones first
   const uint32_t* all_nodes;     // all interior points, deep-interior ones first
   int colour_off[5];             // start of each colour in colour_nodes
+  // chunked colour lists of the FP32 smoother: per colour cc, items
+  // [chunk_off[cc], chunk_mid[cc]) cover up to CHUNK32 deep-interior points
+  // i0, i0 + 4, .. of one line (pack_ijk(i0, j, k) | (count - 1) << 30), items
+  // [chunk_mid[cc], chunk_off[cc + 1]) are single points next to the cell
+  // boundary (pack_ijk)
+  const uint32_t* chunk_nodes;
+  int chunk_off[5], chunk_mid[4];
   // lower primitives: canonical rows 0 .. off_C-1 in sliced ELL (32-row
   // slices, column-major inside a slice), Dirichlet rows have diag 0
   // rows stored in smoother-step order: position p holds canonical row
@@ -83,7 +94,7 @@ struct LevelView {
   const int* low_pos;            // [off_C]
   const T* low_diag;             // [off_C]
   int* err;                      // device error word: set to 1 when a bounded wait gives up
-  int smooth_cfg;                // FP32 surrogate smoother: -1 / -2 = per-colour node kernel (1 / 2 nodes per thread in flight), 0..3 = staged, 4..5 = wavefront
+  int smooth_cfg;                // FP32 surrogate smoother: -1 / -2 = per-colour node kernel (1 / 2 nodes per thread in flight), 0..3 = staged, 4..5 = wavefront, 6 = chunked
   // right-hand sides processed together: vector b of a level lives at
   // v + b vstride, its halo copy at ghost + b gstride, its residual partials
   // at partial + b pstride, its lower-step buffer at tmp + b tstride
@@ -138,9 +149,11 @@ struct Level {
   uint32_t* d_colour_nodes = nullptr;
   uint32_t* d_all_nodes = nullptr;
   int colour_off[5] = {0, 0, 0, 0, 0};
+  uint32_t* d_chunk_nodes = nullptr;   // chunked colour lists (see LevelView)
+  int chunk_off[5] = {0, 0, 0, 0, 0}, chunk_mid[4] = {0, 0, 0, 0};
   // FP32 surrogate smoother chosen by the tuner (TUNE_NONE = not tuned, -1 =
   // per-colour node kernel, -2 = the same with two nodes per thread in flight,
-  // 0..3 = staged, 4..5 = wavefront configuration) and the candidates' times
+  // 0..3 = staged, 4..5 = wavefront, 6 = chunked configuration) and the candidates' times
   // (ms; index cfg + 2)
   int tune32 = TUNE_NONE;
   double tune32_ms[2 + SMOOTH32_CONFIGS] = {};

@@ -17,7 +17,9 @@
 // FP32 smoother.  The cell's per-plane weight polynomials (FP32, paired by
 // direction) are staged in shared memory once per launch and evaluated per
 // node with packed FP32 FMAs (Sec. 3.4).  No thread waits on anything but
-// the CTA barrier.
+// the CTA barrier.  A step's node-list entries and their f values do not
+// depend on u, so each thread loads its first entries of step s + 1 before
+// the barrier that ends step s.
 #include <algorithm>
 
 #include <cuda_runtime.h>
@@ -44,12 +46,70 @@ size_t wave_smem(int N) {
   return sizeof(float2) * (size_t)(N - 3) * NPAIR * npp2<Q>();
 }
 
+// The colour tasks of step s: colour cc on plane s + 1 - 2 cc, as one pool
+// of list entries [0, e4): entries [e_cc, e_cc+1) are task cc, starting at
+// list position b_cc.
+struct Tasks {
+  int b0, b1, b2, b3, e1, e2, e3, e4;
+};
+
+__device__ __forceinline__ Tasks step_tasks(const LevelView<float>& lv, int s, int np) {
+  Tasks t;
+  int e = 0;
+  auto one = [&](int cc, int& b) {
+    const int k = s + 1 - 2 * cc;
+    if (k < 1 || k > np) {
+      b = 0;
+      return;
+    }
+    b = lv.plane_off[k * 4 + cc];
+    e += lv.plane_off[k * 4 + cc + 1] - b;
+  };
+  one(0, t.b0);
+  t.e1 = e;
+  one(1, t.b1);
+  t.e2 = e;
+  one(2, t.b2);
+  t.e3 = e;
+  one(3, t.b3);
+  t.e4 = e;
+  return t;
+}
+
+// A list entry of a step (the point packed, its position in the cell's
+// block of the vector, -1 for none) with its right-hand side, loaded ahead:
+// neither depends on the values the step reads from u.
+struct Entry {
+  uint32_t p;
+  int lin;
+  float fv;
+};
+
+__device__ __forceinline__ Entry load_entry(const LevelView<float>& lv, const Tasks& t, int s, int idx,
+                                            const float* fc) {
+  Entry e;
+  const int cc = (idx >= t.e1) + (idx >= t.e2) + (idx >= t.e3);
+  const int pos = cc == 0 ? t.b0 + idx : (cc == 1 ? t.b1 + idx - t.e1 : (cc == 2 ? t.b2 + idx - t.e2 : t.b3 + idx - t.e3));
+  if (idx < t.e4) {
+    const uint32_t q = lv.plane_nodes[pos];
+    const int k = s + 1 - 2 * cc;
+    e.p = pack_ijk(unpack_i(q), unpack_j(q), k);
+    e.lin = lin_interior32(unpack_i(q), unpack_j(q), k, lv.N);
+    e.fv = fc[e.lin];
+  } else {
+    e.p = 0u;
+    e.lin = -1;
+    e.fv = 0.0f;
+  }
+  return e;
+}
+
 template <int Q, int THREADS>
 __global__ void __launch_bounds__(THREADS, wave_min_blocks<THREADS>()) lsqp_wave32_smooth(LevelView<float> lv,
                                                                                        float* u, const float* f) {
   constexpr int NP = (Q + 1) * (Q + 2) / 2;
   constexpr int NP2 = npp2<Q>();
-  constexpr int B = 2;  // nodes per thread in flight
+  constexpr int B = 2;  // entries per thread in flight
   extern __shared__ __align__(16) float2 s_tab2[];   // [N - 3][NPAIR][NP2]
   const int N = lv.N, np = N - 3;
   const int c = blockIdx.x;
@@ -72,63 +132,59 @@ __global__ void __launch_bounds__(THREADS, wave_min_blocks<THREADS>()) lsqp_wave
   };
   for (int k = 1; k <= 3; ++k) prefetch(u, k);
   for (int k = 1; k <= 2; ++k) prefetch(f, k);
+
+  float* uc = u + cbase;          // the cell's block of u and f
+  const float* fc = f + cbase;
+  // Eq. 5.1 at entry e with its neighbours nb (FP32, paired directions)
+  auto update = [&](const Entry& e, const float (&nb)[14]) {
+    const int i = unpack_i(e.p), j = unpack_j(e.p), k = unpack_k(e.p);
+    const float2* P = s_tab2 + (k - 1) * NPAIR * NP2;
+    const float2 Iv = make_float2((float)i, (float)i), Jv = make_float2((float)j, (float)j);
+    float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int m = 0; m < 7; ++m)
+      acc = __ffma2_rn(eval_plane2<Q>(P + m * NP2, Iv, Jv), make_float2(nb[2 * m], nb[2 * m + 1]), acc);
+    const float wc = eval_plane2<Q>(P + 7 * NP2, Iv, Jv).x;
+    uc[e.lin] = div_nr32(e.fv - acc.x - acc.y, wc);
+  };
+  auto gather = [&](const Entry& e, float (&nb)[14]) {
+    const int i = unpack_i(e.p), j = unpack_j(e.p), k = unpack_k(e.p);
+    if (deep_interior(i, j, k, N)) {
+      int off[14];
+      neighbour_offsets(j, k, N, off);
+#pragma unroll
+      for (int w = 0; w < 14; ++w) nb[w] = uc[e.lin + off[w]];
+    } else {
+#pragma unroll
+      for (int w = 0; w < 14; ++w) nb[w] = load_pt(lv, (const float*)u, c, i + DI(w), j + DJ(w), k + DK(w));
+    }
+  };
+
+  Tasks T = step_tasks(lv, 0, np);
+  Entry ahead[B];
+#pragma unroll
+  for (int b = 0; b < B; ++b) ahead[b] = load_entry(lv, T, 0, threadIdx.x + b * THREADS, fc);
   __syncthreads();
 
   for (int s = 0; s <= np + 5; ++s) {
     prefetch(u, s + 4);
     prefetch(f, s + 3);
-    // the pool of this step's colour tasks: colour cc on plane s + 1 - 2 cc
-    int beg[4], end[5];
-    end[0] = 0;
-#pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-      const int k = s + 1 - 2 * cc;
-      const bool on = k >= 1 && k <= np;
-      beg[cc] = on ? lv.plane_off[k * 4 + cc] : 0;
-      end[cc + 1] = end[cc] + (on ? lv.plane_off[k * 4 + cc + 1] - beg[cc] : 0);
-    }
-    for (int base = threadIdx.x; base < end[4]; base += B * THREADS) {
-      int kk[B], ii[B], jj[B];
-      int64_t I[B];
-      float nb[B][14], fv[B];
-      bool ok[B];
+    for (int base = threadIdx.x; base < T.e4; base += B * THREADS) {
+      Entry e[B];
+      float nb[B][14];
 #pragma unroll
       for (int b = 0; b < B; ++b) {
-        const int idx = base + b * THREADS;
-        ok[b] = idx < end[4];
-        const int cc = (idx >= end[1]) + (idx >= end[2]) + (idx >= end[3]);
-        kk[b] = s + 1 - 2 * cc;
-        const uint32_t p = ok[b] ? lv.plane_nodes[beg[cc] + idx - end[cc]] : pack_ijk(2, 2, 2);
-        ii[b] = unpack_i(p);
-        jj[b] = unpack_j(p);
-        if (!ok[b]) kk[b] = 2;
-        I[b] = cbase + lin_interior32(ii[b], jj[b], kk[b], N);
-        if (!ok[b]) continue;
-        fv[b] = f[I[b]];
-        if (deep_interior(ii[b], jj[b], kk[b], N)) {
-          int off[14];
-          neighbour_offsets(jj[b], kk[b], N, off);
-#pragma unroll
-          for (int w = 0; w < 14; ++w) nb[b][w] = u[I[b] + off[w]];
-        } else {
-#pragma unroll
-          for (int w = 0; w < 14; ++w)
-            nb[b][w] = load_pt(lv, (const float*)u, c, ii[b] + DI(w), jj[b] + DJ(w), kk[b] + DK(w));
-        }
+        e[b] = base == (int)threadIdx.x ? ahead[b] : load_entry(lv, T, s, base + b * THREADS, fc);
+        if (e[b].lin >= 0) gather(e[b], nb[b]);
       }
 #pragma unroll
-      for (int b = 0; b < B; ++b) {
-        if (!ok[b]) continue;
-        const float2* P = s_tab2 + (kk[b] - 1) * NPAIR * NP2;
-        const float2 Iv = make_float2((float)ii[b], (float)ii[b]), Jv = make_float2((float)jj[b], (float)jj[b]);
-        float2 acc = make_float2(0.0f, 0.0f);
-#pragma unroll
-        for (int m = 0; m < 7; ++m)
-          acc = __ffma2_rn(eval_plane2<Q>(P + m * NP2, Iv, Jv), make_float2(nb[b][2 * m], nb[b][2 * m + 1]), acc);
-        const float wc = eval_plane2<Q>(P + 7 * NP2, Iv, Jv).x;
-        u[I[b]] = div_nr32(fv[b] - acc.x - acc.y, wc);
-      }
+      for (int b = 0; b < B; ++b)
+        if (e[b].lin >= 0) update(e[b], nb[b]);
     }
+    // the next step's first entries and their f, before the barrier
+    T = step_tasks(lv, s + 1, np);
+#pragma unroll
+    for (int b = 0; b < B; ++b) ahead[b] = load_entry(lv, T, s + 1, threadIdx.x + b * THREADS, fc);
     __syncthreads();
   }
 }
@@ -145,8 +201,8 @@ void launch_wave(const LevelView<float>& lv, float* u, const float* f, cudaStrea
 
 template <int Q>
 void launch_wave_cfg(int cfg, const LevelView<float>& lv, float* u, const float* f, cudaStream_t st) {
-  if (cfg == 0) launch_wave<Q, 256>(lv, u, f, st);
-  else launch_wave<Q, 512>(lv, u, f, st);
+  if (cfg == 0) launch_wave<Q, 128>(lv, u, f, st);
+  else launch_wave<Q, 256>(lv, u, f, st);
 }
 
 int optin_smem_wave() {

@@ -8,8 +8,12 @@ batched coarse conjugate-gradient solve iterates until every vector has
 converged, so converged vectors take extra iterations; in mixed precision
 those last-digit changes of the FP64 coarse correction flip FP32 roundings
 of the inner cycle); a batched solve reaches 1e-8 for every vector and
-agrees with the oracle's V-cycle on one of them.  nrhs = 5 covers a partial group
-of the 4-vector cell kernels."""
+agrees with the oracle's V-cycle on one of them.  The cell kernels form a
+node's weights once for all right-hand sides of the call; nrhs = 32 (the
+batched configuration's count) is checked per vector against single calls:
+bitwise in FP64 for the surrogate apply and smoother (the same integer
+weights and the same FMA order), 1e-13 for IFEM and the residual norms, the
+FP32 bound in FP32."""
 import numpy as np
 import pytest
 
@@ -80,6 +84,36 @@ def test_batched_operators_match_single(c1, opname, dtype):
     assert rel(R.cpu().numpy(), st(r1), lv.free) <= tol
     assert rel(Us.cpu().numpy(), st(s1), lv.free) <= tol
     assert np.allclose(norms, n1, rtol=max(tol, 1e-12))
+
+
+@pytest.mark.parametrize("dtype", [hhg.HHG_F64, hhg.HHG_F32])
+@pytest.mark.parametrize("opname", ["lsqp", "ifem"])
+def test_batched_32_match_single(c1, opname, dtype):
+    s, n, lv = c1
+    op = OPS[opname]
+    nb = 32
+    dt = np.float64 if dtype == hhg.HHG_F64 else np.float32
+    U = torch.from_numpy(synthetic.batch(n, nb).astype(dt)).cuda()
+    Fv = torch.from_numpy(synthetic.batch(n, nb, "gaussian").astype(dt)).cuda()
+    Y, R, Us = torch.empty_like(U), torch.empty_like(U), U.clone()
+    s.apply(U, Y, op=op, dtype=dtype, nrhs=nb)
+    norms = s.residual(U, Fv, R, op=op, dtype=dtype, nrhs=nb)
+    s.smooth(Fv, Us, 1, op=op, dtype=dtype, nrhs=nb)
+    torch.cuda.synchronize()
+    exact = dtype == hhg.HHG_F64 and opname == "lsqp"
+    for b in (0, 7, 31):
+        y, r, u = torch.empty_like(U[b]), torch.empty_like(U[b]), U[b].clone()
+        s.apply(U[b], y, op=op, dtype=dtype)
+        nr = s.residual(U[b], Fv[b], r, op=op, dtype=dtype)[0]
+        s.smooth(Fv[b], u, 1, op=op, dtype=dtype)
+        torch.cuda.synchronize()
+        for got, ref in ((Y[b], y), (R[b], r), (Us[b], u)):
+            g, e = got.cpu().numpy()[None], ref.cpu().numpy()[None]
+            if exact:
+                assert np.array_equal(g[:, lv.free], e[:, lv.free])
+            else:
+                assert rel(g, e, lv.free) <= TOL[dtype]
+        assert abs(norms[b] - nr) <= max(TOL[dtype], 1e-13) * nr
 
 
 @pytest.mark.parametrize("dtype", [hhg.HHG_F64, hhg.HHG_F32])
