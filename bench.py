@@ -35,6 +35,7 @@ import time
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+T_START = time.perf_counter()
 sys.path.insert(0, ROOT)
 
 METRIC = "GLUP/s surrogate smoother vs IFEM; V-cycle s to 1e-8 residual; p50/p99 latency"
@@ -48,6 +49,8 @@ WORKLOADS = {
                                "r in [0.55, 1]"),
     "shell480_N64": (1, 2, 6, "480 macro cells (icosahedral shell, 1 surface refinement, 2 layers), N=64, "
                               "r in [0.55, 1]"),
+    "shell480_N128": (1, 2, 7, "480 macro cells (icosahedral shell, 1 surface refinement, 2 layers), N=128, "
+                               "r in [0.55, 1]"),
     "shell60_N16": (0, 1, 4, "60 macro cells (icosahedral shell, 1 layer), N=16, r in [0.55, 1]"),
 }
 HBM_FALLBACK_GBS = 6800.0    # profiling recipe's fallback, used only when MEASURED_PEAKS.json is absent
@@ -93,7 +96,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--mode", choices=["solve", "smoother", "serve", "variants", "discretisation", "batch", "peaks",
-                                      "traffic"],
+                                      "traffic", "mixed"],
                    default="solve",
                    help="solve: the whole path per step (default); smoother: finest-level sweeps only "
                         "(for profiling the smoother kernels)")
@@ -105,7 +108,7 @@ def parse():
                    help="f64: FP64 V-cycles; mixed: FP32 V-cycles inside FP64 iterative refinement")
     p.add_argument("--serve-requests", type=int, default=48,
                    help="requests of the serving stream reported beside the solve (0 = skip)")
-    p.add_argument("--serve-batch-rhs", type=int, default=16,
+    p.add_argument("--serve-batch-rhs", type=int, default=8,
                    help="continuous batching of the serving stream: right-hand sides per merged solve (1 = off)")
     p.add_argument("--disc-max-nodes", type=float, default=25e6,
                    help="--mode discretisation: largest level (total nodes) of the study")
@@ -119,6 +122,9 @@ def parse():
                    help="skip the mixed-precision vs FP64 solve on the N=128 shell reported beside the default line")
     p.add_argument("--batch-rhs", type=int, default=32, help="--mode batch: right-hand sides of the batched solve")
     p.add_argument("--nrhs", type=int, default=1, help="--mode smoother: right-hand sides smoothed together")
+    p.add_argument("--fp64-kernel", type=int, default=0, choices=[0, 1, 2],
+                   help="FP64 surrogate kernels: 0 = per node (default), 1 = runs, one launch per colour, "
+                        "2 = runs with the cell-resident sweep")
     p.add_argument("--ncu-report", type=str, default=None,
                    help="--mode traffic: ncu report (.ncu-rep) holding DRAM counters of one launch of the kernel")
     p.add_argument("--traffic-key", type=str, default="lsqp_node_smooth_f64",
@@ -216,7 +222,7 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 
 def traffic_record(kernel: str, workload: str):
-    """ncu DRAM bytes of one sweep (4 colour launches) of `kernel` on
+    """ncu DRAM bytes of one sweep (all its launches) of `kernel` on
     `workload`, if recorded for the current kernel source (profiles/traffic.txt,
     written by profiles/traffic_record.py from an ncu capture); None when
     absent or when the source changed since the capture."""
@@ -242,6 +248,7 @@ def run_ours(args, rank, world, local):
     tang, layers, L, desc = WORKLOADS[args.workload]
     stream = torch.cuda.current_stream()
     s = hhg.Shell(0.55, 1.0, tang, layers, L, stream=stream)
+    hhg.hhg_set_fp64_kernel(s.handle, args.fp64_kernel)
     n_total, n_free = s.num_nodes()
     free_per_level = {l: s.num_nodes(l)[1] for l in range(2, L + 1)}
     f = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_F)).cuda()
@@ -261,13 +268,16 @@ def run_ours(args, rank, world, local):
         per_cycle = sum((nu1 + nu2 + 1) * free_per_level[l] for l in range(3, L + 1)) + free_per_level[L]
         return cycles * per_cycle + free_per_level[L]
 
+    log("shell set up (%d nodes)" % n_total)
     # arithmetic peaks of this GPU, measured now (roofline denominators)
     peaks = measure_peaks(hhg, stream)
+    log("peaks measured")
     hbm_gbs, hbm_note = hbm_peak()
 
     for _ in range(args.warmup):
         step(f, u)
     torch.cuda.synchronize()
+    log("warm-up steps done")
 
     props = torch.cuda.get_device_properties(local)
     uuid = "GPU-" + str(props.uuid) if hasattr(props, "uuid") else None
@@ -314,8 +324,10 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         return n_free * reps / (a.elapsed_time(b) * 1e-3) / 1e9
 
+    log("timed steps done")
     g_lsqp = sweep_glups(hhg.HHG_OP_LSQP, 3)
     g_ifem = sweep_glups(hhg.HHG_OP_IFEM, 1)
+    log("smoother sweeps timed")
     f64_solve = None
     if args.precision == "mixed" and args.compare_f64:
         u.zero_()
@@ -345,21 +357,25 @@ def run_ours(args, rank, world, local):
                "d2h_bytes_per_step": 8 * n_total, "steps": ke}
 
     # the dominant kernel: the finest level's cell-interior smoother, timed
-    # per sweep (4 colour launches, each updating one colour of every cell)
+    # per sweep (one cell-resident launch, or 4 colour launches)
     N = 2 ** L
     n_cells = 20 * 4 ** tang * layers * 3
     units_per_sweep = n_cells * (N - 1) * (N - 2) * (N - 3) // 6
     sweep_s = sm_ms * 1e-3 / max(sm_n, 1)
-    common = {"sweeps": sm_n, "launches": 4 * sm_n, "avg_sweep_ms": sweep_s * 1e3,
-              "avg_launch_ms": sweep_s * 1e3 / 4, "units_per_sweep": units_per_sweep,
-              "units_per_launch": units_per_sweep / 4}
+    k64, lps, tkey = fp64_smoother_name(s, L, args.q)
+    if args.precision == "mixed":
+        cfg32 = hhg.hhg_tuning(s.handle, L)[0]
+        lps = 1 if 0 <= cfg32 <= 5 or cfg32 == 7 else 4
+    common = {"sweeps": sm_n, "launches": lps * sm_n, "avg_sweep_ms": sweep_s * 1e3,
+              "avg_launch_ms": sweep_s * 1e3 / lps, "units_per_sweep": units_per_sweep,
+              "units_per_launch": units_per_sweep / lps}
     if args.precision == "f64":
         achieved = STENCIL_FLOPS * units_per_sweep / sweep_s / 1e12
-        traffic = traffic_record("lsqp_node_smooth_f64", args.workload)
-        roofline = {"kernel": "lsqp_node_kernel<%d,SMOOTH> (finest level; one sweep = 4 colour launches)" % args.q,
+        traffic = traffic_record(tkey, args.workload)
+        roofline = {"kernel": k64,
                     "bound": "alu", "achieved": achieved, "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
                     "frac": achieved / peaks["fp64_tflops"],
-                    "traffic": traffic / 4 if traffic else None,
+                    "traffic": traffic / lps if traffic else None,
                     "peak_note": "of measured: FP64 FMA throughput of this GPU measured in this run "
                                  "(hhg_peak_rate, 2 flops per FMA)",
                     "algorithmic": "29 FP64 flops per update (Eq. 5.1 with known weights: 14 FMA + 1 multiply by "
@@ -370,9 +386,10 @@ def run_ours(args, rank, world, local):
                                             "exact integer arithmetic here, so this rate is not bounded by the FP64 "
                                             "pipe"},
                     "dram": {"algorithmic_gbs": 24 * units_per_sweep / sweep_s / 1e9,
-                             "measured_gbs": (traffic / (sweep_s / 4) / 1e9) if traffic else None,
+                             "measured_gbs": (traffic / sweep_s / 1e9) if traffic else None,
+                             "traffic_per_sweep": traffic,
                              "peak_gbs": hbm_gbs, "peak_note": hbm_note,
-                             "frac": ((traffic / (sweep_s / 4) / 1e9) / hbm_gbs) if traffic else None}}
+                             "frac": ((traffic / sweep_s / 1e9) / hbm_gbs) if traffic else None}}
     else:
         achieved = 12 * units_per_sweep / sweep_s / 1e9
         cfg = hhg.hhg_tuning(s.handle, L)[0]
@@ -405,16 +422,51 @@ def run_ours(args, rank, world, local):
     s.close()
     del f, u
     torch.cuda.empty_cache()
-    if world == 1 and args.precision == "f64" and not args.no_mixed_c3 and args.workload == "shell3840_N64":
-        mp = mixed_vs_f64("shell3840_N128", args.q, args.j)
-        out["mixed_precision"] = mp
-        out["speedup_over_f64_solve"] = mp["speedup_over_f64_solve"]
-        out["speedup_over_f64_solve_workload"] = mp["workload"]
     return out
+
+
+def log(msg):
+    """Progress of the bench on stderr (the JSON line goes to stdout)."""
+    print("[bench %7.1f s] %s" % (time.perf_counter() - T_START, msg), file=sys.stderr, flush=True)
+
+
+def sub_json(extra, timeout_s):
+    """Runs this script again with `extra` arguments in a child process (its
+    own CUDA context, after this process has released its device memory) and
+    returns the last JSON line it prints; a child that fails or runs past
+    timeout_s gives {"error": ...} instead, so the bench line is always
+    printed."""
+    cmd = [sys.executable, os.path.abspath(__file__), *extra]
+    try:
+        res = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s)
+    except subprocess.TimeoutExpired:
+        return {"error": "did not finish within %d s" % timeout_s, "args": extra}
+    lines = [x for x in res.stdout.splitlines() if x.startswith("{")]
+    if res.returncode != 0 or not lines:
+        return {"error": "exit %d: %s" % (res.returncode, res.stderr.strip().splitlines()[-1:] or ""), "args": extra}
+    return json.loads(lines[-1])
+
+
+def fp64_smoother_name(s, L, q):
+    """(name, launches per sweep, traffic-record key) of the FP64 cell
+    smoother the library runs on level L of shell s."""
+    import paper_1608_06473_gb300 as hhg
+    variant, cs = hhg.hhg_fp64_kernel(s.handle, L)
+    if cs:
+        return ("lsqp_resident_sweep<double,%d> (finest level; one launch per sweep, each cell's interior in the "
+                "shared memory of a cluster of %d CTAs)" % (q, cs), 1, "lsqp_resident_f64")
+    if variant == hhg.FP64_NODES:
+        return ("lsqp_node_kernel<%d,SMOOTH> (finest level; one sweep = 4 colour launches)" % q, 4,
+                "lsqp_node_smooth_f64")
+    return ("lsqp_run64_kernel<%d,SMOOTH> (finest level; one sweep = 4 colour launches, a thread per run of a "
+            "line)" % q, 4, "lsqp_run64_smooth_f64")
 
 
 def smoother32_name(cfg, q):
     """The FP32 cell smoother kernel of tuner configuration cfg."""
+    if cfg >= 7:
+        return ("lsqp_resident_sweep<float,%d> (finest level, one launch per sweep, each cell's interior in the "
+                "shared memory of a thread-block cluster)" % q)
     if cfg >= 6:
         return ("lsqp_chunk32_smooth<%d> (finest level, one launch per colour; a thread takes up to 4 points of a "
                 "line)" % q)
@@ -448,6 +500,7 @@ def mixed_vs_f64(workload, q, j):
     out = {"workload": workload, "shell": desc, "nodes": n_total, "unknowns": n_free, "cycle": "V(3,3)",
            "rtol": 1e-8}
     sol = {}
+    log("N = 128 shell set up")
     for name, dtype in (("mixed", hhg.HHG_F32), ("f64", hhg.HHG_F64)):
         uu = torch.zeros_like(f)
         a, b = ev(), ev()
@@ -468,6 +521,7 @@ def mixed_vs_f64(workload, q, j):
         hhg.hhg_timing(s.handle, False)
         out[name] = {"solve_s": a.elapsed_time(b) * 1e-3, "fit_s": fit_s, "cycles": cyc, "relres": float(rel[0]),
                      "cell_sweep_ms": sm_ms / max(sm_n, 1)}
+        log("N = 128 %s solves done" % name)
         sol[name] = uu
     out["speedup_over_f64_solve"] = out["f64"]["solve_s"] / out["mixed"]["solve_s"]
     out["mixed_vs_f64_rel_l2"] = float(torch.linalg.vector_norm(sol["mixed"] - sol["f64"]) /
@@ -604,7 +658,7 @@ SERVE_LEVELS = [4, 5, 6, 7]                          # N = 16 .. 128 on the 60-m
 
 
 def serve_run(n_requests, rate_hz=200.0, seed=2024, max_inflight=4, warm_fraction=0.5, max_batch_rhs=16,
-              hbm_budget_gb=32.0):
+              hbm_budget_gb=96.0):
     """Poisson stream of shell solves through the library's request loop
     (hhg_server_*): levels 4-7 and inner radius (from an 8-point grid in
     [0.35, 0.7]) drawn uniformly, 1-8 right-hand sides uniform[-1, 1] each,
@@ -639,6 +693,7 @@ def serve_run(n_requests, rate_hz=200.0, seed=2024, max_inflight=4, warm_fractio
         for t in ts:
             srv.wait(t)
         st0 = srv.stats()
+        log("serving: %d hierarchies built before the stream" % len(ts))
         for ri, L, nr in reqs:
             rhs(ri, L, nr)
         t0 = time.perf_counter()
@@ -655,6 +710,7 @@ def serve_run(n_requests, rate_hz=200.0, seed=2024, max_inflight=4, warm_fractio
             worst = max(worst, float(rel.max()))
             infos.append(info)
         stats = srv.stats()
+        log("serving: %d requests done" % len(tickets))
     finally:
         srv.close()
     lat = np.array([i["t_end"] - i["t_submit"] for i in infos])
@@ -949,6 +1005,7 @@ def run_smoother(args):
     stream = torch.cuda.current_stream()
     s = hhg.Shell(0.55, 1.0, tang, layers, L, stream=stream)
     n_total, n_free = s.num_nodes()
+    hhg.hhg_set_fp64_kernel(s.handle, args.fp64_kernel)
     opcode = hhg.HHG_OP_LSQP if args.op == "lsqp" else hhg.HHG_OP_IFEM
     if opcode == hhg.HHG_OP_LSQP:
         s.fit(args.q, args.j, stream=stream)
@@ -1001,6 +1058,9 @@ def main():
     if args.mode == "traffic":
         print(json.dumps(run_traffic(args)))
         return
+    if args.mode == "mixed":
+        print(json.dumps(mixed_vs_f64("shell3840_N128", args.q, args.j)))
+        return
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))
         world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
@@ -1009,12 +1069,24 @@ def main():
             print(json.dumps(out))
         return
     rank, world, local = dist_init(args.gpus)
+    log("start: %s" % args.workload)
     out = run_ours(args, rank, world, local)
-    if rank == 0 and world == 1 and args.serve_requests > 0:
-        out["serving"] = serve_run(args.serve_requests, max_batch_rhs=args.serve_batch_rhs)
+    log("solve, smoother and e2e timed")
+    if rank == 0 and world == 1:
+        if args.precision == "f64" and not args.no_mixed_c3 and args.workload == "shell3840_N64":
+            mp = sub_json(["--mode", "mixed", "--q", str(args.q), "--j", str(args.j)], 300)
+            out["mixed_precision"] = mp
+            out["speedup_over_f64_solve"] = mp.get("speedup_over_f64_solve")
+            out["speedup_over_f64_solve_workload"] = mp.get("workload")
+            log("mixed precision at N = 128 done")
+        if args.serve_requests > 0:
+            out["serving"] = sub_json(["--mode", "serve", "--serve-requests", str(args.serve_requests),
+                                       "--serve-batch-rhs", str(args.serve_batch_rhs)], 300)
+            log("serving done")
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.workload)
+            log("cpu baseline done")
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

@@ -383,8 +383,10 @@ hhg_status hhg_timing_read(hhg_shell* shell, int which, double* total_ms, int64_
  * (wavefront skew, threads per CTA) = (1, 256), (1, 1024), (2, 128),
  * (2, 512), 4..5 for the plane-wavefront one-launch kernel (u in place
  * through the caches) with 128 and 256 threads per CTA, 6 for the
- * per-colour kernel over chunks of up to 4 points of a line; -9 if not
- * tuned.  ms (nullable, 9 entries) receives each candidate's best time for one cell
+ * per-colour kernel over chunks of up to 4 points of a line, 7 for the
+ * cell-resident sweep (each cell's interior held in the shared memory of a
+ * cluster of 1..8 CTAs for the four colour steps); -9 if not
+ * tuned.  ms (nullable, 10 entries) receives each candidate's best time for one cell
  * sweep, candidate cfg at ms[cfg + 2] (-1 = not run).  The FP32 apply and
  * residual use the two-nodes variant when the smoother does.  Batched calls
  * (nrhs > 1) smooth with the per-colour kernel that forms every node's
@@ -392,12 +394,31 @@ hhg_status hhg_timing_read(hhg_shell* shell, int which, double* total_ms, int64_
 hhg_status hhg_tuning(const hhg_shell* shell, int L, int* cfg, double* ms);
 
 /* Pins the FP32 surrogate smoother of level L to configuration cfg (-2, -1,
- * a staged configuration 0..3, a wavefront configuration 4..5 or the
- * chunked configuration 6 as above)
+ * a staged configuration 0..3, a wavefront configuration 4..5, the
+ * chunked configuration 6 or the cell-resident configuration 7 as above)
  * until the next fit; a one-launch configuration that does not fit the
  * level falls back to the per-colour kernel at launch.  HHG_EINVAL for an
  * unknown cfg. */
 hhg_status hhg_set_tuning(hhg_shell* shell, int L, int cfg);
+
+/* Kernels of the single-right-hand-side FP64 surrogate apply, residual and
+ * smoother (Sec. 3.4).  variant 0 (the default): a thread per point, each
+ * weight evaluated by integer Horner from the plane table, one launch per
+ * colour.  variant 1: a thread per run of up to 8 points of one line (one
+ * colour, or consecutive points), each weight reached by exact integer
+ * forward differences along the run (Eq. 5.4), one launch per colour.
+ * variant 2: the run kernels, with the smoother's four colour steps as one
+ * cell-resident sweep (each cell's interior held in the shared memory of a
+ * cluster of CTAs) where the cell fits.  All give bitwise the same results;
+ * the choice only changes speed (on a GB300 the default is the fastest).
+ * HHG_EINVAL for another value. */
+hhg_status hhg_set_fp64_kernel(hhg_shell* shell, int variant);
+
+/* The FP64 kernel variant in effect and, for level L, the CTAs per cluster
+ * of the cell-resident smoother sweep (0 when the smoother runs one launch
+ * per colour: another variant, no fit yet, or a cell too large for the
+ * shared memory of 8 CTAs). */
+hhg_status hhg_fp64_kernel(hhg_shell* shell, int L, int* variant, int* cluster);
 
 /* Throughput of one arithmetic pipe on the current device (the paper has
  * no counterpart: these are the roofline denominators of the FP64 and FP32

@@ -101,6 +101,8 @@ _SIGS = {
     "hhg_timing": [_P, _I],
     "hhg_tuning": [_P, _I, ctypes.POINTER(ctypes.c_int), _P],
     "hhg_set_tuning": [_P, _I, _I],
+    "hhg_set_fp64_kernel": [_P, _I],
+    "hhg_fp64_kernel": [_P, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     "hhg_set_graphs": [_P, _I],
     "hhg_timing_read": [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
     "hhg_peak_rate": [_I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _P],
@@ -175,7 +177,7 @@ def hhg_check_arith(which: int, a, b, out, n: int, stream=None):
 def hhg_tuning(shell: int, L: int):
     """(chosen FP32 smoother configuration, per-candidate ms) of level L."""
     cfg = ctypes.c_int()
-    ms = np.zeros(9)
+    ms = np.zeros(10)
     _check(lib().hhg_tuning(shell, L, ctypes.byref(cfg), ms.ctypes.data))
     return cfg.value, ms
 
@@ -186,6 +188,20 @@ def hhg_set_graphs(shell: int, enable: bool):
 
 def hhg_set_tuning(shell: int, L: int, cfg: int):
     _check(lib().hhg_set_tuning(shell, L, cfg))
+
+
+FP64_NODES, FP64_RUNS, FP64_RESIDENT = 0, 1, 2
+
+
+def hhg_set_fp64_kernel(shell: int, variant: int):
+    _check(lib().hhg_set_fp64_kernel(shell, variant))
+
+
+def hhg_fp64_kernel(shell: int, L: int):
+    """(FP64 kernel variant, CTAs per cluster of the resident sweep on level L; 0 = per-colour launches)."""
+    v, cs = ctypes.c_int(), ctypes.c_int()
+    _check(lib().hhg_fp64_kernel(shell, L, ctypes.byref(v), ctypes.byref(cs)))
+    return v.value, cs.value
 
 
 def hhg_last_error() -> str:

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
 LIB = os.path.join(HERE, "libhhg.so")
-SOURCES = ["mesh.cpp", "linalg.cpp", "cell.cu", "stage.cu", "wave.cu", "low.cu", "load.cu", "coarse.cu", "api.cu", "diag.cu", "server.cpp"]
+SOURCES = ["mesh.cpp", "linalg.cpp", "cell.cu", "stage.cu", "wave.cu", "resident.cu", "low.cu", "load.cu", "coarse.cu", "api.cu", "diag.cu", "server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-Xcompiler", "-O2", "--expt-relaxed-constexpr"]

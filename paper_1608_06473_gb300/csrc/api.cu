@@ -270,6 +270,50 @@ static void build_level(hhg_shell* s, int n, cudaStream_t st) {
           if (!deep(i, j, k) && (i + 2 * j + 3 * k) % 4 == cc) chunk_nodes.push_back(pack_ijk(i, j, k));
   }
   L.chunk_off[4] = (int)chunk_nodes.size();
+  // run lists of the FP64 surrogate kernels (see LevelView): per line, the
+  // points of the segment (one colour, stride 4; or all, stride 1) split
+  // where deep-interior and boundary-adjacent points meet, each part into
+  // near-equal runs of at most RUN64 points; deep runs first
+  std::vector<uint2> run_nodes;
+  for (int g = 0; g < 5; ++g) {
+    L.run_off[g] = (int)run_nodes.size();
+    const int h = g < 4 ? 4 : 1;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int k = 1; k < N; ++k)
+        for (int j = 1; j < N - k; ++j) {
+          const int last = N - 1 - j - k;
+          int i = 1;
+          while (g < 4 && i <= last && (i + 2 * j + 3 * k) % 4 != g) i += 1;
+          while (i <= last) {
+            const bool d = deep(i, j, k);
+            int n_pts = 0;
+            while (i + n_pts * h <= last && deep(i + n_pts * h, j, k) == d) ++n_pts;
+            const int n_runs = (n_pts + RUN64 - 1) / RUN64;
+            for (int r = 0, done = 0; r < n_runs; ++r) {
+              const int cnt = (n_pts - done) / (n_runs - r);
+              if (d == (pass == 0))
+                run_nodes.push_back(make_uint2(pack_ijk(i + done * h, j, k), (uint32_t)cnt | ((uint32_t)d << 8)));
+              done += cnt;
+            }
+            i += n_pts * h;
+          }
+        }
+  }
+  L.run_off[5] = (int)run_nodes.size();
+  std::vector<int> run_kidx((size_t)4 * (N + 1) * 2, 0);
+  for (int g = 0; g < 4; ++g) {
+    const int b = L.run_off[g], n_seg = L.run_off[g + 1] - b;
+    int deep_end = 0;
+    while (deep_end < n_seg && (run_nodes[b + deep_end].y & 0x100u)) ++deep_end;
+    for (int part = 0; part < 2; ++part) {
+      const int lo = part == 0 ? 0 : deep_end, hi = part == 0 ? deep_end : n_seg;
+      int e = lo;
+      for (int k = 0; k <= N; ++k) {
+        while (e < hi && unpack_k(run_nodes[b + e].x) < k) ++e;
+        run_kidx[((size_t)g * (N + 1) + k) * 2 + part] = e;
+      }
+    }
+  }
   std::vector<uint32_t> bnd_ijk;
   std::vector<int> bnd_slot;
   boundary_points(N, bnd_ijk, bnd_slot);
@@ -324,6 +368,8 @@ static void build_level(hhg_shell* s, int n, cudaStream_t st) {
   L.d_colour_nodes = upload(A, colour_nodes, st);
   L.d_all_nodes = upload(A, all_nodes, st);
   L.d_chunk_nodes = upload(A, chunk_nodes, st);
+  L.d_run_nodes = upload(A, run_nodes, st);
+  L.d_run_kidx = upload(A, run_kidx, st);
   L.d_bnd_ijk = upload(A, bnd_ijk, st);
   L.d_bnd_slot = upload(A, bnd_slot, st);
   L.d_halo_src = upload(A, halo_src, st);
@@ -436,6 +482,10 @@ LevelView<double> view<double>(hhg_shell* s, int n) {
   v.colour_nodes = L.d_colour_nodes;
   v.all_nodes = L.d_all_nodes;
   for (int cc = 0; cc < 5; ++cc) v.colour_off[cc] = L.colour_off[cc];
+  v.run_nodes = L.d_run_nodes;
+  for (int g = 0; g < 6; ++g) v.run_off[g] = L.run_off[g];
+  v.run_kidx = L.d_run_kidx;
+  v.fp64_kernel = s->fp64_kernel;
   v.sell_ptr = L.d_sell_ptr; v.sell_col = L.d_sell_col; v.sell_val = L.d_sell_val; v.low_diag = L.d_low_diag;
   v.low_perm = L.d_low_perm; v.low_pos = L.d_low_pos;
   v.err = s->d_err;
@@ -464,6 +514,10 @@ LevelView<float> view<float>(hhg_shell* s, int n) {
   v.chunk_nodes = L.d_chunk_nodes;
   for (int cc = 0; cc < 5; ++cc) v.chunk_off[cc] = L.chunk_off[cc];
   for (int cc = 0; cc < 4; ++cc) v.chunk_mid[cc] = L.chunk_mid[cc];
+  v.run_nodes = d.run_nodes;
+  for (int g = 0; g < 6; ++g) v.run_off[g] = d.run_off[g];
+  v.run_kidx = d.run_kidx;
+  v.fp64_kernel = d.fp64_kernel;
   v.sell_ptr = d.sell_ptr; v.sell_col = d.sell_col; v.sell_val = L.d_sell_val32; v.low_diag = L.d_low_diag32;
   v.low_perm = d.low_perm; v.low_pos = d.low_pos;
   v.err = d.err;
@@ -1198,6 +1252,28 @@ hhg_status hhg_set_tuning(hhg_shell* s, int L, int cfg) {
     HHG_CHECK(cfg >= -2 && cfg < SMOOTH32_CONFIGS, HHG_EINVAL, "unknown smoother configuration");
     s->levels[n].tune32 = cfg;
     ++s->gen;
+  });
+}
+
+hhg_status hhg_set_fp64_kernel(hhg_shell* s, int variant) {
+  return guarded([&] {
+    HHG_CHECK(s != nullptr, HHG_EINVAL, "NULL shell");
+    HHG_CHECK(variant == FP64_NODES || variant == FP64_RUNS || variant == FP64_RESIDENT, HHG_EINVAL,
+              "unknown FP64 kernel variant");
+    s->fp64_kernel = variant;
+    ++s->gen;
+  });
+}
+
+hhg_status hhg_fp64_kernel(hhg_shell* s, int L, int* variant, int* cluster) {
+  return guarded([&] {
+    const int n = level_index(s, L);
+    if (variant) *variant = s->fp64_kernel;
+    if (cluster) {
+      LevelView<double> v = view<double>(s, n);
+      v.nrhs = 1;
+      *cluster = s->fp64_kernel == FP64_RESIDENT ? resident_cluster_size(v) : 0;
+    }
   });
 }
 

@@ -42,6 +42,7 @@
 #include "arith.cuh"
 #include "device.cuh"
 #include "kernels.h"
+#include "runs.cuh"
 
 namespace hhg {
 
@@ -159,8 +160,6 @@ __device__ __forceinline__ void batch_norms_out(const double* s_nrm, int nrhs, i
 // memory; thread-per-node application
 // ---------------------------------------------------------------------------
 
-template <int Q>
-constexpr int NPP64 = ((Q + 1) * (Q + 2) / 2 + 1) / 2 * 2;
 
 // E per cell: B = max_w sum_t |A_wt| N^deg(t) bounds every partial sum of
 // the nested Horner evaluation (in j, then in i) of any direction's
@@ -332,6 +331,116 @@ __global__ void __launch_bounds__(NODE_THREADS, 2) lsqp_node_batch_kernel(LevelV
       node_apply_all<double, MODE>(lv, c, i, j, k, w, rc, u, out, f, s_nrm);
     }
     if (MODE == RESIDUAL) batch_norms_out(s_nrm, lv.nrhs, lv.pstride, c, partial);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 surrogate along runs of a line: forward differences in exact integer
+// arithmetic (Sec. 3.4, Eq. 5.4)
+// ---------------------------------------------------------------------------
+
+// 256 threads x 3 CTAs per SM: 80 registers a thread without spills (512 x 2
+// caps them at 64 and spills).
+constexpr int RUN64_THREADS = 256;
+
+// One run of `cnt` points i0, i0 + h, .. of line (j, k) of cell c.  The
+// weights are the same integers as in the per-node kernel, reached by
+// additions instead of multiplies (Q additions per weight and point after a
+// start of (Q + 1)(Q + 2) / 2 + Q (Q + 1) multiply-adds per weight and run),
+// converted and inverted on the integer pipe as there, and applied in the
+// same order, so every result is bitwise that of lsqp_node_kernel.  The
+// direction loop is outermost so only the run's accumulators and one
+// difference table are live.
+template <int Q, Mode MODE, bool DEEP>
+__device__ __forceinline__ void lsqp64_run(const LevelView<double>& lv, const long long* P, int c, int E, int i0,
+                                           int j, int k, int cnt, int h, int64_t I0, double* u, double* out,
+                                           const double* f, double& nrm) {
+  const int N = lv.N;
+  const int L = N - 1 - j - k, m1 = N - 2 - k, m0 = N - 1 - k;
+  const int tc = m1 * (m1 + 1) / 2 - j + 1, bc = -(m0 * (m0 + 1) / 2) + j - 1;
+  double acc[RUN64];
+  long long D[Q + 1];
+  if (MODE == SMOOTH) {
+#pragma unroll
+    for (int s = 0; s < RUN64; ++s)
+      if (s < cnt) acc[s] = f[I0 + s * h];
+  } else {
+    run_start<Q>(P + MC * NPP64<Q>, (unsigned)i0, (unsigned)j, (unsigned)h, D);
+#pragma unroll
+    for (int s = 0; s < RUN64; ++s)
+      if (s < cnt) {
+        acc[s] = i64_to_f64_scaled(D[0], E) * u[I0 + s * h];
+        run_step<Q>(D);
+      }
+  }
+#pragma unroll 1
+  for (int w = 0; w < 14; ++w) {
+    run_start<Q>(P + w * NPP64<Q>, (unsigned)i0, (unsigned)j, (unsigned)h, D);
+    const int off = neighbour_offset(w, L, tc, bc);
+    const int di = DI(w), dj = DJ(w), dk = DK(w);
+#pragma unroll
+    for (int s = 0; s < RUN64; ++s)
+      if (s < cnt) {
+        const double nb =
+            DEEP ? u[I0 + s * h + off] : load_pt(lv, (const double*)u, c, i0 + s * h + di, j + dj, k + dk);
+        const double wt = i64_to_f64_scaled(D[0], E);
+        acc[s] = MODE == SMOOTH ? fma(-wt, nb, acc[s]) : fma(wt, nb, acc[s]);
+        run_step<Q>(D);
+      }
+  }
+  if (MODE == SMOOTH) {
+    run_start<Q>(P + MC * NPP64<Q>, (unsigned)i0, (unsigned)j, (unsigned)h, D);
+#pragma unroll
+    for (int s = 0; s < RUN64; ++s)
+      if (s < cnt) {
+        u[I0 + s * h] = acc[s] * rcp_i64_scaled(D[0], E);
+        run_step<Q>(D);
+      }
+  } else {
+#pragma unroll
+    for (int s = 0; s < RUN64; ++s)
+      if (s < cnt) {
+        if (MODE == APPLY) {
+          out[I0 + s * h] = acc[s];
+        } else {
+          const double r = f[I0 + s * h] - acc[s];
+          out[I0 + s * h] = r;
+          nrm = fma(r, r, nrm);
+        }
+      }
+  }
+}
+
+// FP64 surrogate over a run list (one colour with h = 4, or all interior
+// points with h = 1): one CTA per macro cell, its plane table staged in
+// shared memory, a thread per run.
+template <int Q, Mode MODE>
+__global__ void __launch_bounds__(RUN64_THREADS, 3) lsqp_run64_kernel(LevelView<double> lv,
+                                                                      const uint2* __restrict__ items, int n_items,
+                                                                      int h, double* u, double* out, const double* f,
+                                                                      double* partial) {
+  extern __shared__ __align__(16) long long s_tab64[];   // [N - 3][15][NPP64]
+  const int c = blockIdx.x;
+  const int N = lv.N;
+  load_plane64<Q>(lv, c, s_tab64);
+  const int E = lv.cell_e[c];
+  const int64_t base = lv.off_C + (int64_t)c * lv.n_int;
+  __syncthreads();
+  double nrm = 0.0;
+  for (int t = threadIdx.x; t < n_items; t += blockDim.x) {
+    const uint2 it = items[t];
+    const int i0 = unpack_i(it.x), j = unpack_j(it.x), k = unpack_k(it.x);
+    const int cnt = (int)(it.y & 0xffu);
+    const long long* P = s_tab64 + (k - 1) * 15 * NPP64<Q>;
+    const int64_t I0 = base + lin_interior32(i0, j, k, N);
+    if (it.y & 0x100u)
+      lsqp64_run<Q, MODE, true>(lv, P, c, E, i0, j, k, cnt, h, I0, u, out, f, nrm);
+    else
+      lsqp64_run<Q, MODE, false>(lv, P, c, E, i0, j, k, cnt, h, I0, u, out, f, nrm);
+  }
+  if (MODE == RESIDUAL) {
+    const double tot = block_sum(nrm);
+    if (threadIdx.x == 0) partial[c] = tot;
   }
 }
 
@@ -745,9 +854,38 @@ void launch_node64(const LevelView<double>& lv, const uint32_t* list, int n, dou
   launch_batch<double, MODE>(lsqp_node_batch_kernel<Q, MODE>, lv, table, list, n, u, out, f, partial, st);
 }
 
+// Run-list segment g (colour g = 0..3 with stride 4, or 4 = all interior
+// points with stride 1) through the FP64 run kernel (single right-hand side).
+template <int Q, Mode MODE>
+void launch_run64(const LevelView<double>& lv, int g, double* u, double* out, const double* f, double* partial,
+                  cudaStream_t st) {
+  HHG_CHECK(lv.plane64 != nullptr, HHG_ENOTFIT, "FP64 surrogate plane table missing");
+  const size_t table = sizeof(long long) * (size_t)(lv.N - 3) * 15 * NPP64<Q>;
+  auto kern = lsqp_run64_kernel<Q, MODE>;
+  ensure_smem_limit((const void*)kern, table);
+  kern<<<lv.nC, RUN64_THREADS, table, st>>>(lv, lv.run_nodes + lv.run_off[g], lv.run_off[g + 1] - lv.run_off[g],
+                                            g < 4 ? 4 : 1, u, out, f, partial);
+  HHG_CUDA(cudaGetLastError());
+  count_launch();
+}
+
 template <int Q>
 void lsqp64(const LevelView<double>& lv, Mode mode, double* u, double* out, const double* f, double* partial,
             cudaStream_t st) {
+  if (mode == SMOOTH && lv.fp64_kernel == FP64_RESIDENT && resident_supported(lv)) {
+    launch_resident_sweep<double>(lv, u, f, st);
+    return;
+  }
+  if (lv.nrhs == 1 && lv.fp64_kernel != FP64_NODES) {
+    switch (mode) {
+      case APPLY: launch_run64<Q, APPLY>(lv, 4, u, out, f, partial, st); break;
+      case RESIDUAL: launch_run64<Q, RESIDUAL>(lv, 4, u, out, f, partial, st); break;
+      case SMOOTH:
+        for (int cc = 0; cc < 4; ++cc) launch_run64<Q, SMOOTH>(lv, cc, u, out, f, partial, st);
+        break;
+    }
+    return;
+  }
   switch (mode) {
     case APPLY: launch_node64<Q, APPLY>(lv, lv.all_nodes, (int)lv.n_int, u, out, f, partial, st); break;
     case RESIDUAL: launch_node64<Q, RESIDUAL>(lv, lv.all_nodes, (int)lv.n_int, u, out, f, partial, st); break;
@@ -924,12 +1062,14 @@ void launch_cell<float>(const LevelView<float>& lv, int op, Mode mode, float* u,
         launch_stage32_smooth(lv, u, f, cfg, st);
       } else if (cfg < STAGE32_CONFIGS + WAVE32_CONFIGS) {
         launch_wave32_smooth(lv, u, f, cfg - STAGE32_CONFIGS, st);
-      } else {
+      } else if (cfg < STAGE32_CONFIGS + WAVE32_CONFIGS + CHUNK32_CONFIGS) {
         switch (lv.q) {
           case 1: chunk32_sweep<1>(lv, u, f, st); break;
           case 2: chunk32_sweep<2>(lv, u, f, st); break;
           default: chunk32_sweep<3>(lv, u, f, st); break;
         }
+      } else {
+        launch_resident_sweep<float>(lv, u, f, st);
       }
       return;
     }

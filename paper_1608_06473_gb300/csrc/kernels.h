@@ -58,14 +58,31 @@ void launch_wave32_smooth(const LevelView<float>& lv, float* u, const float* f, 
 // one launch over all cells.
 constexpr int CHUNK32_CONFIGS = 1;
 bool chunk32_supported(const LevelView<float>& lv);
-static_assert(STAGE32_CONFIGS + WAVE32_CONFIGS + CHUNK32_CONFIGS == SMOOTH32_CONFIGS, "tuner table size");
+
+// Cell-resident sweep (resident.cu): the four cell colour steps of the
+// surrogate smoother in one launch, each cell's interior held in the shared
+// memory of a cluster of 1..8 CTAs (FP64, and FP32 configuration 7).
+// Supported for one right-hand side when the surrogate is fitted and the
+// largest slab fits one CTA's shared memory.  A bounded wait that gives up
+// sets *lv.err and leaves u unchanged.
+constexpr int RESIDENT32_CONFIGS = 1;
+template <class T>
+bool resident_supported(const LevelView<T>& lv);
+template <class T>
+void launch_resident_sweep(const LevelView<T>& lv, T* u, const T* f, cudaStream_t st);
+// Cluster size (CTAs per cell) the sweep uses on this level, 0 if unsupported.
+template <class T>
+int resident_cluster_size(const LevelView<T>& lv);
+static_assert(STAGE32_CONFIGS + WAVE32_CONFIGS + CHUNK32_CONFIGS + RESIDENT32_CONFIGS == SMOOTH32_CONFIGS,
+              "tuner table size");
 
 // Whether smoother configuration cfg >= 0 (staged 0..3, wavefront 4..5,
-// chunked 6) can run on this level and vector.
+// chunked 6, cell-resident 7) can run on this level and vector.
 inline bool smooth32_supported(const LevelView<float>& lv, const float* u, int cfg) {
   if (cfg < STAGE32_CONFIGS) return stage32_supported(lv, u, cfg);
   if (cfg < STAGE32_CONFIGS + WAVE32_CONFIGS) return wave32_supported(lv, cfg - STAGE32_CONFIGS);
-  return chunk32_supported(lv);
+  if (cfg < STAGE32_CONFIGS + WAVE32_CONFIGS + CHUNK32_CONFIGS) return chunk32_supported(lv);
+  return resident_supported(lv);
 }
 
 // FP64 surrogate plane table (fit time): per cell the scale exponent E and,

@@ -14,8 +14,8 @@ namespace hhg {
 
 // FP32 surrogate smoother configurations the tuner chooses from besides the
 // per-colour node kernels: 0..3 staged (stage.cu), 4..5 wavefront (wave.cu),
-// 6 chunked per-colour (cell.cu)
-constexpr int SMOOTH32_CONFIGS = 7;
+// 6 chunked per-colour (cell.cu), 7 cell-resident sweep (resident.cu)
+constexpr int SMOOTH32_CONFIGS = 8;
 constexpr int TUNE_NONE = -9;           // FP32 smoother of a level not tuned yet
 
 // Geometry of one macro cell: its 4 vertices (ascending global id) and the
@@ -40,6 +40,14 @@ struct Allocator {
 
 // Deep-interior points per chunked work item of the FP32 smoother.
 constexpr int CHUNK32 = 4;
+// Most points per run item of the FP64 surrogate kernels (run lists below).
+constexpr int RUN64 = 8;
+// FP64 surrogate kernel variants (hhg_set_fp64_kernel): weights per node by
+// Horner (default, the fastest measured), or by forward differences along
+// runs of a line, one launch per colour or as the cell-resident sweep.
+constexpr int FP64_NODES = 0;       // per-node kernels
+constexpr int FP64_RUNS = 1;        // per-colour run kernels
+constexpr int FP64_RESIDENT = 2;    // run kernels, smoother as the cell-resident sweep where it fits
 
 // Packed cell-local point: i | j << 10 | k << 20 (N <= 1023).
 HD uint32_t pack_ijk(int i, int j, int k) { return (uint32_t)i | ((uint32_t)j << 10) | ((uint32_t)k << 20); }
@@ -83,6 +91,19 @@ struct LevelView {
   // boundary (pack_ijk)
   const uint32_t* chunk_nodes;
   int chunk_off[5], chunk_mid[4];
+  // run lists of the FP64 surrogate kernels: segment g = 0..3 holds the runs
+  // of colour g (points i0, i0 + 4, ..), segment 4 the runs over all interior
+  // points (i0, i0 + 1, ..), items [run_off[g], run_off[g + 1]).  A run is
+  // up to RUN64 points of one line (j, k), all deep-interior or all next to
+  // the cell boundary, deep runs first: x = pack_ijk(i0, j, k),
+  // y = count | deep << 8
+  const uint2* run_nodes;
+  int run_off[6];
+  // run_kidx[(g (N + 1) + k) 2 + part]: first item of colour g's runs
+  // (relative to run_off[g]) among the deep (part 0) or boundary-adjacent
+  // (part 1) runs whose plane is >= k, k = 0 .. N
+  const int* run_kidx;
+  int fp64_kernel;               // FP64_NODES, FP64_RUNS or FP64_RESIDENT
   // lower primitives: canonical rows 0 .. off_C-1 in sliced ELL (32-row
   // slices, column-major inside a slice), Dirichlet rows have diag 0
   // rows stored in smoother-step order: position p holds canonical row
@@ -94,7 +115,7 @@ struct LevelView {
   const int* low_pos;            // [off_C]
   const T* low_diag;             // [off_C]
   int* err;                      // device error word: set to 1 when a bounded wait gives up
-  int smooth_cfg;                // FP32 surrogate smoother: -1 / -2 = per-colour node kernel (1 / 2 nodes per thread in flight), 0..3 = staged, 4..5 = wavefront, 6 = chunked
+  int smooth_cfg;                // FP32 surrogate smoother: -1 / -2 = per-colour node kernel (1 / 2 nodes per thread in flight), 0..3 = staged, 4..5 = wavefront, 6 = chunked, 7 = cell-resident
   // right-hand sides processed together: vector b of a level lives at
   // v + b vstride, its halo copy at ghost + b gstride, its residual partials
   // at partial + b pstride, its lower-step buffer at tmp + b tstride
@@ -151,6 +172,9 @@ struct Level {
   int colour_off[5] = {0, 0, 0, 0, 0};
   uint32_t* d_chunk_nodes = nullptr;   // chunked colour lists (see LevelView)
   int chunk_off[5] = {0, 0, 0, 0, 0}, chunk_mid[4] = {0, 0, 0, 0};
+  uint2* d_run_nodes = nullptr;        // FP64 run lists (see LevelView)
+  int run_off[6] = {0, 0, 0, 0, 0, 0};
+  int* d_run_kidx = nullptr;
   // FP32 surrogate smoother chosen by the tuner (TUNE_NONE = not tuned, -1 =
   // per-colour node kernel, -2 = the same with two nodes per thread in flight,
   // 0..3 = staged, 4..5 = wavefront, 6 = chunked configuration) and the candidates' times
@@ -213,6 +237,7 @@ struct hhg_shell {
   // coarse-solver iteration count it was captured with, and a generation
   // counter bumped whenever captured kernels or buffers change
   bool graphs = true;
+  int fp64_kernel = hhg::FP64_NODES;  // FP64 surrogate kernel variant (hhg_set_fp64_kernel)
   int64_t gen = 0;
   int cg_fixed = 0;          // > 0 while capturing: fixed-count coarse iterations
   int cg_graph_iters = 0;    // iterations the next capture uses

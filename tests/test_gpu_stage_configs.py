@@ -2,7 +2,8 @@
 per-colour thread-per-node kernel with one or two nodes per thread in
 flight, the shared-memory staged one-launch kernel at wavefront skew 1 and
 2 with its CTA sizes, the plane-wavefront one-launch kernel with 128 and
-256 threads, and the per-colour kernel over line chunks) against the FP64
+256 threads, the per-colour kernel over line chunks, and the cell-resident
+sweep with clusters of 1 (N <= 64) and 8 CTAs (N = 128)) against the FP64
 oracle, on the 60-macro shell at N = 16 (whole vector) and N = 32 / 64
 (sampled cells, the FP32 bound of test_gpu_f32: 2e-5 relative, and the
 per-node bound of gpu_checks: C = 128 for two sweeps, 64 for one), pinned
@@ -25,7 +26,7 @@ pytestmark = pytest.mark.gpu
 import paper_1608_06473_gb300 as hhg  # noqa: E402
 
 TOL32 = 2e-5
-CONFIGS = [-2, -1, 0, 1, 2, 3, 4, 5, 6]
+CONFIGS = [-2, -1, 0, 1, 2, 3, 4, 5, 6, 7]
 
 
 def rel(a, b):
