@@ -414,6 +414,21 @@ hhg_status hhg_set_tuning(hhg_shell* shell, int L, int cfg);
  * HHG_EINVAL for another value. */
 hhg_status hhg_set_fp64_kernel(hhg_shell* shell, int variant);
 
+/* Host-side tables of the run and cell-resident kernels (the paper has no
+ * counterpart; no GPU work, for host-side tests).  hhg_run_lists: the run
+ * lists of a cell at N (4 <= N <= 1023): items (nullable, 2 uint32 per run,
+ * cap runs) = packed (i0 | j << 10 | k << 20, count | deep << 8); off6 (6
+ * ints) = start of colour 0..3 (points i0, i0 + 4, ..) and of all points
+ * (i0, i0 + 1, ..), off6[5] = total; kidx (nullable, 8 (N + 1) ints) = per
+ * colour g, plane k = 0..N and part (0 deep-interior runs, 1 runs next to
+ * the cell boundary) the first run of the part on a plane >= k, relative to
+ * off6[g]; *n_items (nullable) = the number of runs.  HHG_EINVAL for N out
+ * of range or a buffer too small.  hhg_slab_planes: the planes [k_bounds[r],
+ * k_bounds[r + 1]) held by cluster rank r of the cell-resident sweep with
+ * `cluster` CTAs per cell (1..8), k_bounds of cluster + 1 ints. */
+hhg_status hhg_run_lists(int N, uint32_t* items, int64_t cap, int* off6, int* kidx, int64_t* n_items);
+hhg_status hhg_slab_planes(int N, int cluster, int* k_bounds);
+
 /* The FP64 kernel variant in effect and, for level L, the CTAs per cluster
  * of the cell-resident smoother sweep (0 when the smoother runs one launch
  * per colour: another variant, no fit yet, or a cell too large for the

@@ -103,6 +103,8 @@ _SIGS = {
     "hhg_set_tuning": [_P, _I, _I],
     "hhg_set_fp64_kernel": [_P, _I],
     "hhg_fp64_kernel": [_P, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+    "hhg_run_lists": [_I, _P, ctypes.c_int64, _P, _P, ctypes.POINTER(ctypes.c_int64)],
+    "hhg_slab_planes": [_I, _I, _P],
     "hhg_set_graphs": [_P, _I],
     "hhg_timing_read": [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
     "hhg_peak_rate": [_I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _P],
@@ -195,6 +197,24 @@ FP64_NODES, FP64_RUNS, FP64_RESIDENT = 0, 1, 2
 
 def hhg_set_fp64_kernel(shell: int, variant: int):
     _check(lib().hhg_set_fp64_kernel(shell, variant))
+
+
+def hhg_run_lists(N: int):
+    """(items as an (n, 2) uint32 array, off6, kidx as a (4, N + 1, 2) array) of a cell at N (host only)."""
+    n = ctypes.c_int64()
+    off = np.zeros(6, dtype=np.int32)
+    _check(lib().hhg_run_lists(N, None, 0, off.ctypes.data, None, ctypes.byref(n)))
+    items = np.zeros((n.value, 2), dtype=np.uint32)
+    kidx = np.zeros((4, N + 1, 2), dtype=np.int32)
+    _check(lib().hhg_run_lists(N, items.ctypes.data, n.value, off.ctypes.data, kidx.ctypes.data, ctypes.byref(n)))
+    return items, off, kidx
+
+
+def hhg_slab_planes(N: int, cluster: int):
+    """Plane bounds (cluster + 1 values) of the cell-resident sweep's slabs (host only)."""
+    kb = np.zeros(cluster + 1, dtype=np.int32)
+    _check(lib().hhg_slab_planes(N, cluster, kb.ctypes.data))
+    return kb
 
 
 def hhg_fp64_kernel(shell: int, L: int):

@@ -180,6 +180,57 @@ static void lower_incidence(const MacroMesh& m, const LevelLayout& lay, const st
     if (halo_src[t] >= 0) inc_cb[fill[halo_src[t]]++] = (int)t;
 }
 
+// Run lists of the FP64 surrogate kernels and the cell-resident sweep (see
+// LevelView): per line, the points of the segment (one colour, stride 4; or
+// all, stride 1) split where deep-interior and boundary-adjacent points
+// meet, each part into near-equal runs of at most RUN64 points; deep runs
+// first, each part in plane order; kidx[(g (N + 1) + k) 2 + part] = first
+// item of colour g (relative to off[g]) of the part whose plane is >= k.
+// Host only (also reached through hhg_run_lists for host-side tests).
+static void build_run_lists(int N, std::vector<uint2>& run_nodes, int off[6], std::vector<int>& run_kidx) {
+  auto deep = [N](int i, int j, int k) { return i >= 2 && j >= 2 && k >= 2 && i + j + k <= N - 2; };
+  run_nodes.clear();
+  for (int g = 0; g < 5; ++g) {
+    off[g] = (int)run_nodes.size();
+    const int h = g < 4 ? 4 : 1;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int k = 1; k < N; ++k)
+        for (int j = 1; j < N - k; ++j) {
+          const int last = N - 1 - j - k;
+          int i = 1;
+          while (g < 4 && i <= last && (i + 2 * j + 3 * k) % 4 != g) i += 1;
+          while (i <= last) {
+            const bool d = deep(i, j, k);
+            int n_pts = 0;
+            while (i + n_pts * h <= last && deep(i + n_pts * h, j, k) == d) ++n_pts;
+            const int n_runs = (n_pts + RUN64 - 1) / RUN64;
+            for (int r = 0, done = 0; r < n_runs; ++r) {
+              const int cnt = (n_pts - done) / (n_runs - r);
+              if (d == (pass == 0))
+                run_nodes.push_back(make_uint2(pack_ijk(i + done * h, j, k), (uint32_t)cnt | ((uint32_t)d << 8)));
+              done += cnt;
+            }
+            i += n_pts * h;
+          }
+        }
+  }
+  off[5] = (int)run_nodes.size();
+  run_kidx.assign((size_t)4 * (N + 1) * 2, 0);
+  for (int g = 0; g < 4; ++g) {
+    const int b = off[g], n_seg = off[g + 1] - b;
+    int deep_end = 0;
+    while (deep_end < n_seg && (run_nodes[b + deep_end].y & 0x100u)) ++deep_end;
+    for (int part = 0; part < 2; ++part) {
+      const int lo = part == 0 ? 0 : deep_end, hi = part == 0 ? deep_end : n_seg;
+      int e = lo;
+      for (int k = 0; k <= N; ++k) {
+        while (e < hi && unpack_k(run_nodes[b + e].x) < k) ++e;
+        run_kidx[((size_t)g * (N + 1) + k) * 2 + part] = e;
+      }
+    }
+  }
+}
+
 static void build_level(hhg_shell* s, int n, cudaStream_t st) {
   const MacroMesh& m = s->mesh;
   Level& L = s->levels[n];
@@ -270,50 +321,9 @@ static void build_level(hhg_shell* s, int n, cudaStream_t st) {
           if (!deep(i, j, k) && (i + 2 * j + 3 * k) % 4 == cc) chunk_nodes.push_back(pack_ijk(i, j, k));
   }
   L.chunk_off[4] = (int)chunk_nodes.size();
-  // run lists of the FP64 surrogate kernels (see LevelView): per line, the
-  // points of the segment (one colour, stride 4; or all, stride 1) split
-  // where deep-interior and boundary-adjacent points meet, each part into
-  // near-equal runs of at most RUN64 points; deep runs first
   std::vector<uint2> run_nodes;
-  for (int g = 0; g < 5; ++g) {
-    L.run_off[g] = (int)run_nodes.size();
-    const int h = g < 4 ? 4 : 1;
-    for (int pass = 0; pass < 2; ++pass)
-      for (int k = 1; k < N; ++k)
-        for (int j = 1; j < N - k; ++j) {
-          const int last = N - 1 - j - k;
-          int i = 1;
-          while (g < 4 && i <= last && (i + 2 * j + 3 * k) % 4 != g) i += 1;
-          while (i <= last) {
-            const bool d = deep(i, j, k);
-            int n_pts = 0;
-            while (i + n_pts * h <= last && deep(i + n_pts * h, j, k) == d) ++n_pts;
-            const int n_runs = (n_pts + RUN64 - 1) / RUN64;
-            for (int r = 0, done = 0; r < n_runs; ++r) {
-              const int cnt = (n_pts - done) / (n_runs - r);
-              if (d == (pass == 0))
-                run_nodes.push_back(make_uint2(pack_ijk(i + done * h, j, k), (uint32_t)cnt | ((uint32_t)d << 8)));
-              done += cnt;
-            }
-            i += n_pts * h;
-          }
-        }
-  }
-  L.run_off[5] = (int)run_nodes.size();
-  std::vector<int> run_kidx((size_t)4 * (N + 1) * 2, 0);
-  for (int g = 0; g < 4; ++g) {
-    const int b = L.run_off[g], n_seg = L.run_off[g + 1] - b;
-    int deep_end = 0;
-    while (deep_end < n_seg && (run_nodes[b + deep_end].y & 0x100u)) ++deep_end;
-    for (int part = 0; part < 2; ++part) {
-      const int lo = part == 0 ? 0 : deep_end, hi = part == 0 ? deep_end : n_seg;
-      int e = lo;
-      for (int k = 0; k <= N; ++k) {
-        while (e < hi && unpack_k(run_nodes[b + e].x) < k) ++e;
-        run_kidx[((size_t)g * (N + 1) + k) * 2 + part] = e;
-      }
-    }
-  }
+  std::vector<int> run_kidx;
+  build_run_lists(N, run_nodes, L.run_off, run_kidx);
   std::vector<uint32_t> bnd_ijk;
   std::vector<int> bnd_slot;
   boundary_points(N, bnd_ijk, bnd_slot);
@@ -1262,6 +1272,32 @@ hhg_status hhg_set_fp64_kernel(hhg_shell* s, int variant) {
               "unknown FP64 kernel variant");
     s->fp64_kernel = variant;
     ++s->gen;
+  });
+}
+
+hhg_status hhg_run_lists(int N, uint32_t* items, int64_t cap, int* off6, int* kidx, int64_t* n_items) {
+  return guarded([&] {
+    HHG_CHECK(N >= 4 && N <= 1023 && off6 != nullptr, HHG_EINVAL, "need 4 <= N <= 1023 and off6");
+    std::vector<uint2> runs;
+    std::vector<int> kx;
+    build_run_lists(N, runs, off6, kx);
+    if (n_items) *n_items = (int64_t)runs.size();
+    if (items) {
+      HHG_CHECK(cap >= (int64_t)runs.size(), HHG_EINVAL, "run-list buffer too small");
+      for (size_t t = 0; t < runs.size(); ++t) {
+        items[2 * t] = runs[t].x;
+        items[2 * t + 1] = runs[t].y;
+      }
+    }
+    if (kidx) std::copy(kx.begin(), kx.end(), kidx);
+  });
+}
+
+hhg_status hhg_slab_planes(int N, int cluster, int* k_bounds) {
+  return guarded([&] {
+    HHG_CHECK(N >= 8 && N <= 1023 && cluster >= 1 && cluster <= 8 && k_bounds != nullptr, HHG_EINVAL,
+              "need 8 <= N <= 1023, 1 <= cluster <= 8 and k_bounds");
+    resident_slab_planes(N, cluster, k_bounds);
   });
 }
 

@@ -70,6 +70,9 @@ template <class T>
 bool resident_supported(const LevelView<T>& lv);
 template <class T>
 void launch_resident_sweep(const LevelView<T>& lv, T* u, const T* f, cudaStream_t st);
+// Planes [k_bounds[r], k_bounds[r + 1]) of slab r, r < CS, of a cell at N
+// (host; the kernel computes the same split).
+void resident_slab_planes(int N, int CS, int* k_bounds);
 // Cluster size (CTAs per cell) the sweep uses on this level, 0 if unsupported.
 template <class T>
 int resident_cluster_size(const LevelView<T>& lv);

@@ -416,6 +416,15 @@ bool resident_supported(const LevelView<T>& lv) {
 template bool resident_supported<double>(const LevelView<double>&);
 template bool resident_supported<float>(const LevelView<float>&);
 
+void resident_slab_planes(int N, int CS, int* k_bounds) {
+  for (int r = 0; r < CS; ++r) {
+    int k0, k1;
+    slab_planes(N, CS, r, k0, k1);
+    k_bounds[r] = k0;
+    k_bounds[r + 1] = k1;
+  }
+}
+
 template <class T>
 int resident_cluster_size(const LevelView<T>& lv) {
   if (!resident_supported(lv)) return 0;
