@@ -590,14 +590,15 @@ def host_info():
     return {"nproc": os.cpu_count(), "cpu_model": model}
 
 
-def oracle_c1_vcycle():
+def oracle_c1_vcycle(N=16):
     """Seconds of one V(3,3) cycle of the full oracle (global CSR operators,
-    sparse direct coarse solve) on the 60-cell shell at N = 16, LSQP q = 2,
-    from u = 0 with the seed-0 right-hand side (hierarchy assembly excluded)."""
+    sparse direct coarse solve) on the 60-cell shell at N (16 by default),
+    LSQP q = 2, from u = 0 with the seed-0 right-hand side (hierarchy
+    assembly excluded)."""
     import synthetic
     from oracle import mesh as M
     from oracle import mg
-    H = mg.build_hierarchy(M.make_shell(), 16, "lsqp", 2, 2)
+    H = mg.build_hierarchy(M.make_shell(), N, "lsqp", 2, 2)
     n = H.levels[-1].n_total
     f = synthetic.uniform(n, synthetic.SEED_F)
     t0 = time.perf_counter()
@@ -627,7 +628,10 @@ def cpu_baseline(workload, n_cells=6, sweeps=60):
                           "sample": f"{cores} spawned processes, each {sweeps} sweeps over one seeded macro cell "
                                     f"of {workload}; total updates / slowest process's sweep time"},
             "c1_vcycle_s": oracle_c1_vcycle(),
-            "c1_vcycle_note": "one V(3,3) cycle of the full oracle, 60 cells, N = 16, LSQP q = 2 (one core)"}
+            "c1_vcycle_note": "one V(3,3) cycle of the full oracle, 60 cells, N = 16, LSQP q = 2 (one core)",
+            "shell60_N32_vcycle_s": oracle_c1_vcycle(32),
+            "shell60_N32_vcycle_note": "one V(3,3) cycle of the full oracle, 60 cells, N = 32 (337,986 nodes), "
+                                       "LSQP q = 2 (one core; hierarchy assembly excluded)"}
 
 
 def run_reference(args, rank, world):
