@@ -443,7 +443,8 @@ def sub_json(extra, timeout_s):
         return {"error": "did not finish within %d s" % timeout_s, "args": extra}
     lines = [x for x in res.stdout.splitlines() if x.startswith("{")]
     if res.returncode != 0 or not lines:
-        return {"error": "exit %d: %s" % (res.returncode, res.stderr.strip().splitlines()[-1:] or ""), "args": extra}
+        tail = res.stderr.strip().splitlines()
+        return {"error": "exit %d: %s" % (res.returncode, tail[-1] if tail else ""), "args": extra}
     return json.loads(lines[-1])
 
 

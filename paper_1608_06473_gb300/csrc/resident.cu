@@ -344,14 +344,15 @@ __global__ void __launch_bounds__(RES_THREADS<T>, 1) lsqp_resident_sweep(LevelVi
   for (int64_t p = P0 + threadIdx.x; p < P1; p += blockDim.x) u[cbase + p] = us[p - P0 + sh];
 }
 
-template <class T>
+// Opt-in shared memory per CTA of the current device (queried once; the
+// static's initialisation is thread-safe for the server's worker threads).
 int max_smem_optin() {
-  static int v = 0;
-  if (v == 0) {
-    int dev = 0;
+  static const int v = [] {
+    int dev = 0, bytes = 0;
     HHG_CUDA(cudaGetDevice(&dev));
-    HHG_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  }
+    HHG_CUDA(cudaDeviceGetAttribute(&bytes, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    return bytes;
+  }();
   return v;
 }
 
@@ -360,7 +361,7 @@ int max_smem_optin() {
 template <class T, int Q>
 int resident_cluster(int N, size_t* smem) {
   if (N < 8) return 0;
-  const size_t cap = (size_t)max_smem_optin<T>() - 1024;   // headroom for static shared memory
+  const size_t cap = (size_t)max_smem_optin() - 1024;   // headroom for static shared memory
   for (int CS = 1; CS <= 8; CS *= 2) {
     size_t mx = 0;
     bool ok = true;
