@@ -221,6 +221,18 @@ class ClockSampler:
 # our arm
 # ----------------------------------------------------------------------------
 
+def source_hash(path):
+    """Hash of a CUDA source's code: comments removed and whitespace
+    collapsed, so the traffic record survives documentation edits but not a
+    change to the code it was captured from."""
+    import re
+    src = open(path, encoding="utf-8").read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    src = " ".join(src.split())
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
+
+
 def traffic_record(kernel: str, workload: str):
     """ncu DRAM bytes of one sweep (all its launches) of `kernel` on
     `workload`, if recorded for the current kernel source (profiles/traffic.txt,
@@ -232,8 +244,7 @@ def traffic_record(kernel: str, workload: str):
     rec = json.load(open(path)).get(f"{kernel}@{workload}")
     if not rec:
         return None
-    src = open(os.path.join(ROOT, "paper_1608_06473_gb300", "csrc", rec["source"]), "rb").read()
-    if hashlib.sha256(src).hexdigest()[:16] != rec["sha256_16"]:
+    if source_hash(os.path.join(ROOT, "paper_1608_06473_gb300", "csrc", rec["source"])) != rec["code_sha256_16"]:
         return None
     return rec["dram_bytes_per_sweep"]
 
@@ -962,7 +973,8 @@ def run_traffic(args):
     (profiles/traffic.txt): dram__bytes_read.sum + dram__bytes_write.sum of
     the first launch in an ncu report, times --traffic-scale (launches per
     sweep x the bench workload's units over the captured launch's), keyed by
-    kernel and workload and gated by the hash of the kernel's source file."""
+    kernel and workload and gated by the hash of the kernel source's code
+    (comments and whitespace excluded)."""
     import csv
     import io
     res = subprocess.run(["ncu", "-i", args.ncu_report, "--page", "raw", "--csv"], capture_output=True, text=True,
@@ -972,11 +984,12 @@ def run_traffic(args):
     scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
     val = lambda name: float(first[hdr.index(name)]) * scale[units[hdr.index(name)]]
     per_launch = val("dram__bytes_read.sum") + val("dram__bytes_write.sum")
-    src = open(os.path.join(ROOT, "paper_1608_06473_gb300", "csrc", args.traffic_source), "rb").read()
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     recs = json.load(open(path)) if os.path.exists(path) else {}
     key = f"{args.traffic_key}@{args.workload}"
-    recs[key] = {"source": args.traffic_source, "sha256_16": hashlib.sha256(src).hexdigest()[:16],
+    recs[key] = {"source": args.traffic_source,
+                 "code_sha256_16": source_hash(os.path.join(ROOT, "paper_1608_06473_gb300", "csrc",
+                                                            args.traffic_source)),
                  "dram_bytes_per_sweep": per_launch * args.traffic_scale,
                  "captured_launch_bytes": per_launch, "scale": args.traffic_scale,
                  "kernel": first[hdr.index("Kernel Name")] if "Kernel Name" in hdr else None,

@@ -346,7 +346,7 @@ constexpr int RUN64_THREADS = 256;
 // One run of `cnt` points i0, i0 + h, .. of line (j, k) of cell c.  The
 // weights are the same integers as in the per-node kernel, reached by
 // additions instead of multiplies (Q additions per weight and point after a
-// start of (Q + 1)(Q + 2) / 2 + Q (Q + 1) multiply-adds per weight and run),
+// start of Q (Q + 1) / 2 + Q (Q + 1) multiply-adds per weight and run),
 // converted and inverted on the integer pipe as there, and applied in the
 // same order, so every result is bitwise that of lsqp_node_kernel.  The
 // direction loop is outermost so only the run's accumulators and one
