@@ -109,3 +109,54 @@ def test_rejects_bad_arguments():
     assert hhg.hhg_last_error() != ""
     hhg.hhg_slab_planes(64, 2)   # a successful call clears the message
     assert hhg.hhg_last_error() == ""
+
+
+# Direction offsets (i, j, k) of the 14 neighbours (the order of the stencil
+# weights: me mw mn ms mnw mse tc tw ts tse bc be bn bnw).
+DIRS = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (-1, 1, 0), (1, -1, 0), (0, 0, 1), (-1, 0, 1), (0, -1, 1),
+        (1, -1, 1), (0, 0, -1), (1, 0, -1), (0, 1, -1), (-1, 1, -1)]
+
+
+def lin_interior(i, j, k, N):
+    """Position of interior point (i, j, k) in its cell's block (i fastest,
+    then j, then k)."""
+    tet = lambda n: (n + 1) * (n + 2) * (n + 3) // 6
+    M, a, b, c = N - 4, i - 1, j - 1, k - 1
+    m = M - c
+    return tet(M) - tet(M - c) + b * (m + 1) - b * (b - 1) // 2 + a
+
+
+@pytest.mark.parametrize("N,cluster", [(16, 1), (16, 4), (32, 2), (32, 8), (64, 8)])
+def test_resident_sweep_reads_stay_in_the_owning_slab(N, cluster):
+    """The cell-resident sweep keeps slab r (planes [k_r, k_{r+1})) of a cell
+    in CTA r's shared memory and reads a neighbour on plane k - 1 (k + 1)
+    from CTA r - 1 (r + 1) only when k is the slab's first (last) plane.
+    Every interior neighbour of every run point of the slab must then lie in
+    the slab chosen for it, and every point's update lands in its own slab;
+    boundary neighbours come from the halo."""
+    items, off, kidx = hhg.hhg_run_lists(N)
+    kb = hhg.hhg_slab_planes(N, cluster)
+    start = [lin_interior(1, 1, k, N) for k in range(1, N - 1)] + [lin_interior(1, 1, N - 2, N)]
+    pos0 = lambda k: start[k - 1]   # first position of plane k (plane N - 2 starts at n_int)
+    for r in range(cluster):
+        k0, k1 = int(kb[r]), int(kb[r + 1])
+        for g in range(4):
+            seg = items[off[g]:off[g + 1]]
+            d0, d1, n0, n1 = kidx[g, k0, 0], kidx[g, k1, 0], kidx[g, k0, 1], kidx[g, k1, 1]
+            for x, y in list(seg[d0:d1]) + list(seg[n0:n1]):
+                i0, j, k = int(x & 1023), int((x >> 10) & 1023), int(x >> 20)
+                assert k0 <= k < k1
+                lo = r - 1 if k == k0 else r
+                hi = r + 1 if k + 1 == k1 else r
+                for s in range(int(y & 0xFF)):
+                    i = i0 + 4 * s
+                    assert pos0(k0) <= lin_interior(i, j, k, N) < pos0(k1)
+                    for di, dj, dk in DIRS:
+                        i2, j2, k2 = i + di, j + dj, k + dk
+                        if not (i2 >= 1 and j2 >= 1 and k2 >= 1 and i2 + j2 + k2 <= N - 1):
+                            assert not (y & 0x100)   # deep points have interior neighbours only
+                            continue
+                        owner = lo if dk < 0 else (hi if dk > 0 else r)
+                        assert 0 <= owner < cluster
+                        p = lin_interior(i2, j2, k2, N)
+                        assert pos0(int(kb[owner])) <= p < pos0(int(kb[owner + 1])), (r, owner, (i2, j2, k2))
