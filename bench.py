@@ -356,6 +356,9 @@ def run_ours(args, rank, world, local):
         fh = torch.from_numpy(synthetic.uniform(n_total, synthetic.SEED_F)).pin_memory()
         ke = max(1, min(args.steps, 5))
         uhs = [torch.zeros(n_total, dtype=torch.float64).pin_memory() for _ in range(ke)]   # u0 = 0 per step
+        # one untimed step through host buffers first: the library allocates
+        # its device staging buffers for host vectors on the first such call
+        step(fh, torch.zeros(n_total, dtype=torch.float64).pin_memory())
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         e_upd = 0
@@ -365,7 +368,7 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         te = max_over_ranks(time.perf_counter() - t0, world)
         e2e = {"value": e_upd * world / te / 1e9, "unit": "GLUP/s", "h2d_bytes_per_step": 16 * n_total,
-               "d2h_bytes_per_step": 8 * n_total, "steps": ke}
+               "d2h_bytes_per_step": 8 * n_total, "steps": ke, "warmup": 1}
 
     # the dominant kernel: the finest level's cell-interior smoother, timed
     # per sweep (one cell-resident launch, or 4 colour launches)

@@ -425,7 +425,8 @@ hhg_status hhg_set_fp64_kernel(hhg_shell* shell, int variant);
  * off6[g]; *n_items (nullable) = the number of runs.  HHG_EINVAL for N out
  * of range or a buffer too small.  hhg_slab_planes: the planes [k_bounds[r],
  * k_bounds[r + 1]) held by cluster rank r of the cell-resident sweep with
- * `cluster` CTAs per cell (1..8), k_bounds of cluster + 1 ints. */
+ * `cluster` CTAs per cell (1..8) at N (8 <= N <= 1023), k_bounds of
+ * cluster + 1 ints; HHG_EINVAL otherwise. */
 hhg_status hhg_run_lists(int N, uint32_t* items, int64_t cap, int* off6, int* kidx, int64_t* n_items);
 hhg_status hhg_slab_planes(int N, int cluster, int* k_bounds);
 
