@@ -244,7 +244,7 @@ def traffic_record(kernel: str, workload: str):
     rec = json.load(open(path)).get(f"{kernel}@{workload}")
     if not rec:
         return None
-    if source_hash(os.path.join(ROOT, "paper_1608_06473_gb300", "csrc", rec["source"])) != rec["code_sha256_16"]:
+    if source_hash(os.path.join(ROOT, "paper_1608_06473_gb300", "csrc", rec["source"])) != rec.get("code_sha256_16"):
         return None
     return rec["dram_bytes_per_sweep"]
 
